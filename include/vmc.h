@@ -1,0 +1,194 @@
+/*
+ * vmc.h -- C ABI of libvmc: the data-parallel hot path of CNN variational
+ * Monte Carlo for the spin-1/2 J1-J2 Heisenberg model on an L x L periodic
+ * square lattice (arXiv:2108.13830), on one sm_103a GPU.
+ *
+ * Model (Sec. 2.1, Eq. 3):  H = J1/4 sum_<ij> sigma_i.sigma_j
+ *                             + J2/4 sum_<<ij>> sigma_i.sigma_j.
+ * Wavefunction (Sec. 2.2, Eq. 8-9): W(S) = (-1)^{M_A} W_CNN(S), with
+ * W_CNN a stack of 3x3 circular-padded convolutions -- a 1 -> C embedding,
+ * then D layers C -> C, SiLU after every layer but the last -- and product
+ * pooling of the last layer: log|W_CNN| = sum_{c,p} log|z_{c,p}|,
+ * sgn W_CNN = prod sgn z_{c,p}.  M_A counts up spins on the sublattice
+ * x + y even.
+ *
+ * Conventions shared by every call:
+ *  - Spin configurations are int8 in {+1, -1}, row-major [B][L][L]
+ *    (site i = y * L + x).  L must be even and 4 <= L <= 32.
+ *  - The flat parameter vector theta holds, for l = 0..D, the weights
+ *    W_l[c_out][c_in][ky][kx] followed by the biases b_l[c_out]; c_in = 1 for
+ *    l = 0 and C otherwise.  n = 10 C + D (9 C^2 + C).
+ *    z_l[co][y][x] = b_l[co] + sum W_l[co][ci][ky][kx] a[ci][(y+ky-1) mod L][(x+kx-1) mod L].
+ *  - Every pointer named *_dev is device memory owned by the caller; the
+ *    library never frees or retains it past the call.  Every call is
+ *    asynchronous on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) unless it says otherwise.
+ *  - Return values: VMC_OK, or a negative code.  A negative code from an
+ *    asynchronous call reports argument or launch errors only; faults found
+ *    on the device (non-finite values, timeouts) are read with
+ *    vmc_sync_status().  No call throws across the ABI and no call traps on
+ *    the device.  vmc_last_error() gives a one-line message.
+ *  - The library allocates its own workspaces (cudaMalloc) at vmc_create,
+ *    vmc_set_params or the first call at a given batch size; calls made
+ *    during CUDA-graph capture must not be the first at their size.
+ */
+#ifndef VMC_H_
+#define VMC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VMC_OK             0
+#define VMC_ERR_ARG       -1   /* invalid argument (null pointer, bad size, ...) */
+#define VMC_ERR_CUDA      -2   /* a CUDA runtime call failed */
+#define VMC_ERR_NONFINITE -3   /* some sample produced a non-finite value */
+#define VMC_ERR_TIMEOUT   -4   /* a device-side wait ran out of its time budget */
+#define VMC_ERR_STATE     -5   /* call out of order (e.g. parameters not set) */
+#define VMC_ERR_UNSUPPORTED -6 /* device or configuration not supported */
+
+/* Arithmetic of the convolutions.  VMC_BF16 runs the C -> C and embedding
+ * convolutions on tcgen05 tensor cores with BF16 operands and FP32
+ * accumulation; log|psi| sums, amplitude ratios and E_loc sums are FP64 in
+ * every precision. */
+#define VMC_FP64 0
+#define VMC_FP32 1
+#define VMC_BF16 2
+
+typedef struct vmc_ctx vmc_ctx;
+
+typedef struct {
+    int n_layers_cc;     /* D >= 1: number of C -> C layers after the 1 -> C embedding */
+    int channels;        /* C: 4..64, multiple of 4 (multiple of 16 for VMC_BF16) */
+    int precision;       /* VMC_FP64 | VMC_FP32 | VMC_BF16 */
+    int marshall_sign;   /* 1: include (-1)^{M_A} (Eq. 9) in the sign and E_loc */
+} vmc_arch;
+
+/* Tile choices of the tensor-core forward (chosen by vmc_autotune or set
+ * explicitly).  0 fields mean "library default". */
+typedef struct {
+    int slab_configs;    /* configurations laid side by side in one slab */
+    int slabs;           /* slabs in flight per CTA (1 or 2) */
+    int ctas_per_sm;     /* persistent CTAs per SM */
+} vmc_tiles;
+
+/* Create a context for L x L lattices with couplings J1, J2 (Eq. 3) and the
+ * network `arch`.  Binds the current CUDA device.  *out receives the
+ * context; on failure *out is NULL and the return code says why
+ * (VMC_ERR_UNSUPPORTED when precision is VMC_BF16 and the device is not
+ * sm_103). */
+int vmc_create(int L, double J1, double J2, const vmc_arch *arch, vmc_ctx **out);
+void vmc_destroy(vmc_ctx *ctx);
+
+/* n, the length of the flat parameter vector. */
+int vmc_num_params(const vmc_ctx *ctx, int64_t *n);
+
+/* Copy theta (n values of `dtype`: VMC_FP64 or VMC_FP32, device memory)
+ * into the context and derive the per-precision weight images.  Ordered
+ * on `stream`; theta_dev may be reused after the call returns only once
+ * the stream has passed this point. */
+int vmc_set_params(vmc_ctx *ctx, const void *theta_dev, int dtype, void *stream);
+
+/* Copy the context's FP64 parameter vector (n doubles) to theta_dev. */
+int vmc_get_params(const vmc_ctx *ctx, double *theta_dev, void *stream);
+
+/* log|psi(sigma_b)| and its sign for B configurations (Sec. 2.2, Eq. 8-9).
+ * sigma_dev: int8 [B][L][L].  logabs_dev: double [B].  sign_dev: int8 [B]
+ * (+1, -1, or 0 where psi = 0, in which case logabs = -inf).  B = 0 is a
+ * no-op. */
+int vmc_logpsi(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B,
+               double *logabs_dev, int8_t *sign_dev, void *stream);
+
+/* Local energy E_loc(sigma_b) = sum_{sigma'} H(sigma, sigma') psi(sigma')/psi(sigma)
+ * (Eq. 4-5), summed over the diagonal term and every configuration reached
+ * by exchanging an antiparallel J1 or J2 bond (Sec. 3.1, Fig. 2c: right and
+ * below neighbours for J1, the two lower diagonals for J2).  Each
+ * neighbour sigma' is generated on chip from its parent; the parent is
+ * evaluated in the same launch and the same arithmetic as its neighbours.
+ * eloc_dev: double [B] (total energy, not per site).  n_nbr_dev: int32 [B]
+ * number of exchange neighbours, or NULL.  A sample whose psi is 0 or
+ * non-finite gets NaN and raises VMC_ERR_NONFINITE in vmc_sync_status. */
+int vmc_local_energy(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B,
+                     double *eloc_dev, int32_t *n_nbr_dev, void *stream);
+
+/* The same over a ragged batch of mixed lattice sizes with the context's
+ * weights (translation-invariant convolutions apply to any L).  Sample b has
+ * side L_dev[b] (even, 4 <= L_dev[b] <= L_max) and spins at
+ * packed_dev[offs_dev[b] .. offs_dev[b] + L_dev[b]^2).  L_max is a host
+ * value bounding every L_dev[b]; a sample beyond it gets NaN and raises
+ * VMC_ERR_ARG in vmc_sync_status.  One persistent launch covers the batch. */
+int vmc_local_energy_ragged(vmc_ctx *ctx, const int8_t *packed_dev, const int64_t *offs_dev,
+                            const int32_t *L_dev, int64_t B, int L_max,
+                            double *eloc_dev, int32_t *n_nbr_dev, void *stream);
+
+/* Per-sample log-derivatives O_bk = d log|psi(sigma_b)| / d theta_k (Eq. 5),
+ * by a hand-written backward pass that recomputes the forward activations
+ * (workspace bounded by the number of resident CTAs, not by B).
+ * O_dev: [B][n] row-major of `dtype` (VMC_FP32; VMC_FP64 also allowed for
+ * FP64 contexts).  Runs in FP64 for VMC_FP64 contexts, FP32 otherwise. */
+int vmc_log_derivs(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B,
+                   void *O_dev, int dtype, void *stream);
+
+/* SR moments (Eq. 5): Obar_k = (1/m) sum_b O_bk, Ebar = (1/m) sum_b E_b,
+ * G_k = (1/m) sum_b O_bk (E_b - Ebar).  O_dev float [m][n], E_dev double [m],
+ * outputs double (device).  Sums carry FP64 accuracy. */
+int vmc_sr_moments(vmc_ctx *ctx, const float *O_dev, const double *E_dev, int64_t m,
+                   double *Obar_dev, double *Ebar_dev, double *G_dev, void *stream);
+
+/* out = (S + shift I) v with S v = (1/m) O^T (O v) - Obar (Obar . v), the
+ * covariance of Eq. 7 applied without forming it (Sec. 3.2.2 builds
+ * M = O^T O - <O>^T <O> + shift I).  Computed as
+ * (1/m) O^T (t - tbar) with t = O v, tbar = (1/m) sum_b t_b. */
+int vmc_sr_matvec(vmc_ctx *ctx, const float *O_dev, int64_t m, const double *Obar_dev,
+                  const double *v_dev, double shift, double *out_dev, void *stream);
+
+/* out = O^T w, i.e. out_k = sum_b O_bk w_b, with FP64 accuracy.  O_dev
+ * float [m][n], w_dev double [m], out_dev double [n].  This is the
+ * vector-Jacobian product of log|psi| (the backward of the autograd layer:
+ * d/dtheta sum_b w_b log|psi_b| = O^T w). */
+int vmc_ot_vec(vmc_ctx *ctx, const float *O_dev, int64_t m, const double *w_dev,
+               double *out_dev, void *stream);
+
+/* Solve (S + shift I) x = G for the SR direction (Eq. 6 with eta = 1:
+ * Delta = x; the caller applies theta -= eta x) by conjugate gradient from
+ * x = 0, exactly `iters` iterations (fewer only when the residual is exactly
+ * zero), the recurrence in FP64 and every S v matrix-free.  The iteration is
+ * captured once in a CUDA graph and replayed.  x_dev: double [n].
+ * resid_out (host, nullable): ||r|| / ||G|| after the last step; when it is
+ * non-NULL the call synchronises `stream`. */
+int vmc_sr_solve(vmc_ctx *ctx, const float *O_dev, const double *eloc_dev, int64_t m,
+                 double shift, int iters, double *x_dev, double *resid_out, void *stream);
+
+/* Synchronise `stream` and read (then clear) the device status word:
+ * VMC_OK, VMC_ERR_NONFINITE (with *nonfinite = number of samples, if
+ * non-NULL), VMC_ERR_TIMEOUT or VMC_ERR_ARG. */
+int vmc_sync_status(vmc_ctx *ctx, void *stream, int64_t *nonfinite);
+
+/* Time budget, in nanoseconds, of every device-side wait (mbarrier waits
+ * of the tensor-core pipeline).  0 restores the default (2 s).  A wait that
+ * runs out sets VMC_ERR_TIMEOUT, releases its resources and returns. */
+int vmc_set_wait_budget(vmc_ctx *ctx, int64_t ns);
+
+/* Launch one wait on an mbarrier that nothing arrives on, with the given
+ * budget; the wait must give up and report VMC_ERR_TIMEOUT through
+ * vmc_sync_status.  Exercises the timeout path without faulting the GPU. */
+int vmc_debug_wait_timeout(vmc_ctx *ctx, int64_t budget_ns, void *stream);
+
+/* Tile choice of the tensor-core forward for lattice side L: set, read, or
+ * tune (times each candidate on `probe_B` synthetic configurations with
+ * CUDA events on `stream`, keeps the fastest; synchronises `stream`). */
+int vmc_set_tiles(vmc_ctx *ctx, int L, const vmc_tiles *tiles);
+int vmc_get_tiles(const vmc_ctx *ctx, int L, vmc_tiles *tiles);
+int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream);
+
+/* Kernel launches issued by the last public call (for launch accounting). */
+int64_t vmc_last_launch_count(const vmc_ctx *ctx);
+
+const char *vmc_last_error(const vmc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VMC_H_ */

@@ -1,0 +1,482 @@
+// Stochastic Reconfiguration (Eq. 5-7, Sec. 3.2.2): moments, the
+// matrix-free covariance product and a conjugate-gradient solve.
+//
+// O is FP32 [m][n].  Every product and sum over O is carried in
+// "double-float" arithmetic -- an unevaluated pair (hi, lo) of FP32 values
+// with error-free TwoProduct (FMA) and TwoSum steps (Dekker 1971; Knuth,
+// TAOCP vol. 2) -- which keeps FP64-level accuracy while running on the
+// FP32 pipes; the vector recurrences of CG are plain FP64.
+//
+// S v = (1/m) O^T (O v) - Obar (Obar . v) is evaluated as
+// (1/m) O^T (t - tbar 1) with t = O v and tbar = (1/m) sum_b t_b, which is
+// the same quantity (Obar . v = tbar).
+#include <algorithm>
+#include "vmc_internal.h"
+
+namespace vmc {
+
+struct DF { float h, l; };
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    e = b - (s - a);
+}
+// acc += x * (yh + yl), x exact in FP32
+__device__ __forceinline__ void df_mac(DF &acc, float x, float yh, float yl)
+{
+    const float p = x * yh;
+    float pe = fmaf(x, yh, -p);
+    pe = fmaf(x, yl, pe);
+    float s, e;
+    two_sum(acc.h, p, s, e);
+    e += acc.l + pe;
+    fast_two_sum(s, e, acc.h, acc.l);
+}
+// acc += x
+__device__ __forceinline__ void df_add(DF &acc, float x)
+{
+    float s, e;
+    two_sum(acc.h, x, s, e);
+    e += acc.l;
+    fast_two_sum(s, e, acc.h, acc.l);
+}
+// a += b
+__device__ __forceinline__ void df_add_df(DF &a, const DF &b)
+{
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    e += a.l + b.l;
+    fast_two_sum(s, e, a.h, a.l);
+}
+__device__ __forceinline__ DF df_shfl_xor(const DF &a, int o)
+{
+    DF r;
+    r.h = __shfl_xor_sync(0xffffffffu, a.h, o);
+    r.l = __shfl_xor_sync(0xffffffffu, a.l, o);
+    return r;
+}
+__device__ __forceinline__ void split(double v, float &h, float &l)
+{
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+// Deterministic FP64 block sum (blockDim.x a multiple of 32, <= 1024).
+__device__ double block_sum(double v, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (lane == 0) sh[32] = r;
+    }
+    __syncthreads();
+    return sh[32];
+}
+
+// ---------------------------------------------------------------- moments
+
+// One CTA: mean of a length-m vector, and the centred, scaled pair split
+// out[b] = split(scale * (x_b - mean)).
+__global__ void center_kernel(const double *__restrict__ x, int64_t m, double scale,
+                              double *mean_out, float *oh, float *ol)
+{
+    __shared__ double sh[33];
+    double acc = 0.0;
+    for (int64_t b = threadIdx.x; b < m; b += blockDim.x) acc += x[b];
+    const double mean = block_sum(acc, sh) / (double)m;
+    if (threadIdx.x == 0 && mean_out) *mean_out = mean;
+    for (int64_t b = threadIdx.x; b < m; b += blockDim.x) split(scale * (x[b] - mean), oh[b], ol[b]);
+}
+
+// Column sums over a chunk of rows: part1 = sum O_bk, part2 = sum O_bk w_b.
+// Thread = 4 consecutive columns (VEC) or 1 column.
+template <bool VEC, bool TWO>
+__global__ void colsum_kernel(const float *__restrict__ O, int64_t m, int64_t n, int64_t rows_per_chunk,
+                              const float *__restrict__ wh, const float *__restrict__ wl,
+                              double *part1, double *part2)
+{
+    const int64_t chunk = blockIdx.y;
+    const int64_t r0 = chunk * rows_per_chunk;
+    const int64_t r1 = min(m, r0 + rows_per_chunk);
+    constexpr int V = VEC ? 4 : 1;
+    const int64_t c0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * V;
+    if (c0 >= n) return;
+    DF s1[V], s2[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) { s1[j] = DF{0.f, 0.f}; s2[j] = DF{0.f, 0.f}; }
+    for (int64_t b = r0; b < r1; ++b) {
+        float o[V];
+        if constexpr (VEC) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(O + b * n + c0));
+            o[0] = f.x; o[1] = f.y; o[2] = f.z; o[3] = f.w;
+        } else {
+            o[0] = __ldg(O + b * n + c0);
+        }
+        const float h = TWO ? wh[b] : 0.f, l = TWO ? wl[b] : 0.f;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            if (part1) df_add(s1[j], o[j]);
+            if (TWO) df_mac(s2[j], o[j], h, l);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        if (part1) part1[chunk * n + c0 + j] = (double)s1[j].h + (double)s1[j].l;
+        if (TWO) part2[chunk * n + c0 + j] = (double)s2[j].h + (double)s2[j].l;
+    }
+}
+
+// out[k] = scale * sum_chunks part[c][k] (+ add[k] * add_scale)
+__global__ void reduce_chunks_kernel(const double *__restrict__ part, int nchunk, int64_t n, double scale,
+                                     const double *__restrict__ add, double add_scale, double *out)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < nchunk; ++c) acc += part[(int64_t)c * n + k];
+        acc *= scale;
+        if (add) acc += add_scale * add[k];
+        out[k] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- S v
+
+__global__ void split_kernel(const double *__restrict__ v, int64_t n, float *vh, float *vl)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        split(v[k], vh[k], vl[k]);
+}
+
+// t_b = sum_k O_bk v_k, one warp per row.
+template <bool VEC>
+__global__ void rowdot_kernel(const float *__restrict__ O, int64_t m, int64_t n,
+                              const float *__restrict__ vh, const float *__restrict__ vl, double *t)
+{
+    const int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= m) return;
+    const float *o = O + row * n;
+    DF acc{0.f, 0.f};
+    if (VEC) {
+        const float4 *o4 = reinterpret_cast<const float4 *>(o);
+        const float4 *h4 = reinterpret_cast<const float4 *>(vh);
+        const float4 *l4 = reinterpret_cast<const float4 *>(vl);
+        for (int64_t q = lane; q < n / 4; q += 32) {
+            const float4 a = __ldg(o4 + q), h = __ldg(h4 + q), l = __ldg(l4 + q);
+            df_mac(acc, a.x, h.x, l.x);
+            df_mac(acc, a.y, h.y, l.y);
+            df_mac(acc, a.z, h.z, l.z);
+            df_mac(acc, a.w, h.w, l.w);
+        }
+    } else {
+        for (int64_t k = lane; k < n; k += 32) df_mac(acc, __ldg(o + k), vh[k], vl[k]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const DF other = df_shfl_xor(acc, off);
+        df_add_df(acc, other);
+    }
+    if (lane == 0) t[row] = (double)acc.h + (double)acc.l;
+}
+
+// ---------------------------------------------------------------- CG
+
+// q = u + shift p; partial dot p.q per CTA
+__global__ void cg_q_kernel(const double *__restrict__ part, int nchunk, int64_t n, double shift,
+                            const double *__restrict__ p, double *q, double *pq_part)
+{
+    __shared__ double sh[33];
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double u = 0.0;
+        for (int c = 0; c < nchunk; ++c) u += part[(int64_t)c * n + k];
+        const double qk = u + shift * p[k];
+        q[k] = qk;
+        acc += p[k] * qk;
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) pq_part[blockIdx.x] = s;
+}
+
+__device__ double sum_parts(const double *parts, int np)
+{
+    double s = 0.0;
+    for (int i = 0; i < np; ++i) s += parts[i];
+    return s;
+}
+
+// alpha = rr / pq; x += alpha p; r -= alpha q; partial r.r
+__global__ void cg_update_kernel(const double *__restrict__ pq_part, int np, const double *rr_in,
+                                 double *x, double *r, const double *__restrict__ p,
+                                 const double *__restrict__ q, int64_t n, double *rr_part)
+{
+    __shared__ double sh[33];
+    const double rr = *rr_in;
+    const double pq = sum_parts(pq_part, np);
+    const double alpha = (rr == 0.0 || pq == 0.0) ? 0.0 : rr / pq;
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        x[k] += alpha * p[k];
+        const double rk = r[k] - alpha * q[k];
+        r[k] = rk;
+        acc += rk * rk;
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) rr_part[blockIdx.x] = s;
+}
+
+// beta = rr_new / rr_old; p = r + beta p; split p; rr_out = rr_new
+__global__ void cg_dir_kernel(const double *__restrict__ rr_part, int np, const double *rr_old,
+                              double *rr_out, const double *__restrict__ r, double *p, int64_t n,
+                              float *ph, float *pl)
+{
+    const double rn = sum_parts(rr_part, np);
+    const double ro = *rr_old;
+    const double beta = (ro == 0.0) ? 0.0 : rn / ro;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double pk = r[k] + beta * p[k];
+        p[k] = pk;
+        split(pk, ph[k], pl[k]);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *rr_out = rn;
+}
+
+// x = 0, r = p = G, split p, partial G.G
+__global__ void cg_init_kernel(const double *__restrict__ G, int64_t n, double *x, double *r, double *p,
+                               float *ph, float *pl, double *gg_part)
+{
+    __shared__ double sh[33];
+    double acc = 0.0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double g = G[k];
+        x[k] = 0.0; r[k] = g; p[k] = g;
+        split(g, ph[k], pl[k]);
+        acc += g * g;
+    }
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) gg_part[blockIdx.x] = s;
+}
+
+__global__ void finalize_scalar_kernel(const double *__restrict__ parts, int np, double *out0, double *out1)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const double s = sum_parts(parts, np);
+        *out0 = s;
+        if (out1) *out1 = s;
+    }
+}
+
+__global__ void resid_kernel(const double *rr, const double *gg, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *out = (*gg > 0.0) ? sqrt(*rr / *gg) : 0.0;
+}
+
+// ---------------------------------------------------------------- workspace
+
+struct SrWs {
+    float *vh, *vl;        // [n]
+    float *wh, *wl;        // [m]
+    double *t;             // [m]
+    double *part1, *part2; // [nchunk][n]
+    double *Obar, *G;      // [n]
+    double *r, *p, *q;     // [n]
+    double *scal;          // scalars: 0 Ebar, 1 tbar, 2 gg, 3..4 rr[2], 5 resid
+    double *pq_part, *rr_part, *gg_part;   // [NPART]
+};
+constexpr int NPART = 256;
+
+static int64_t nchunks_for(int64_t m) { return m >= 1024 ? 16 : (m >= 64 ? 4 : 1); }
+
+static int sr_workspace(vmc_ctx *ctx, int64_t m, SrWs *w)
+{
+    const int64_t n = ctx->n, nch = nchunks_for(m);
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t off[16], tot = 0;
+    size_t sz[] = {n * 4, n * 4, (size_t)m * 4, (size_t)m * 4, (size_t)m * 8, (size_t)nch * n * 8, (size_t)nch * n * 8,
+                   (size_t)n * 8, (size_t)n * 8, (size_t)n * 8, (size_t)n * 8, (size_t)n * 8, 64 * 8,
+                   NPART * 8, NPART * 8, NPART * 8};
+    for (int i = 0; i < 16; ++i) { off[i] = tot; tot += al(sz[i]); }
+    int rc = vmc_ensure_ws(ctx, &ctx->sr_ws, &ctx->sr_ws_bytes, tot);
+    if (rc) return rc;
+    char *b = static_cast<char *>(ctx->sr_ws);
+    w->vh = (float *)(b + off[0]); w->vl = (float *)(b + off[1]);
+    w->wh = (float *)(b + off[2]); w->wl = (float *)(b + off[3]);
+    w->t = (double *)(b + off[4]);
+    w->part1 = (double *)(b + off[5]); w->part2 = (double *)(b + off[6]);
+    w->Obar = (double *)(b + off[7]); w->G = (double *)(b + off[8]);
+    w->r = (double *)(b + off[9]); w->p = (double *)(b + off[10]); w->q = (double *)(b + off[11]);
+    w->scal = (double *)(b + off[12]);
+    w->pq_part = (double *)(b + off[13]); w->rr_part = (double *)(b + off[14]); w->gg_part = (double *)(b + off[15]);
+    return VMC_OK;
+}
+
+static bool vec_ok(const float *O, int64_t n) { return (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(O) & 15) == 0); }
+
+// launches the moment kernels; Ebar goes to *Ebar (device)
+static void launch_moments(vmc_ctx *ctx, const float *O, const double *E, int64_t m, const SrWs &w,
+                           double *Obar, double *Ebar, double *G, cudaStream_t s)
+{
+    const int64_t n = ctx->n, nch = nchunks_for(m);
+    const int64_t rpc = (m + nch - 1) / nch;
+    center_kernel<<<1, 1024, 0, s>>>(E, m, 1.0, Ebar, w.wh, w.wl);
+    const bool vec = vec_ok(O, n);
+    const int V = vec ? 4 : 1;
+    dim3 grid((unsigned)((n / V + 127) / 128), (unsigned)nch);
+    if (vec) colsum_kernel<true, true><<<grid, 128, 0, s>>>(O, m, n, rpc, w.wh, w.wl, w.part1, w.part2);
+    else colsum_kernel<false, true><<<grid, 128, 0, s>>>(O, m, n, rpc, w.wh, w.wl, w.part1, w.part2);
+    const int rg = (int)std::min<int64_t>((n + 255) / 256, 4 * ctx->sm_count);
+    reduce_chunks_kernel<<<rg, 256, 0, s>>>(w.part1, (int)nch, n, 1.0 / (double)m, nullptr, 0.0, Obar);
+    reduce_chunks_kernel<<<rg, 256, 0, s>>>(w.part2, (int)nch, n, 1.0 / (double)m, nullptr, 0.0, G);
+    ctx->launches += 4;
+}
+
+// u-partials of S p: rowdot, centre, column dots (p already split into vh/vl)
+static void launch_sv_partials(vmc_ctx *ctx, const float *O, int64_t m, const SrWs &w, cudaStream_t s)
+{
+    const int64_t n = ctx->n, nch = nchunks_for(m);
+    const int64_t rpc = (m + nch - 1) / nch;
+    const bool vec = vec_ok(O, n);
+    const unsigned rows_grid = (unsigned)((m + 7) / 8);
+    if (vec) rowdot_kernel<true><<<rows_grid, 256, 0, s>>>(O, m, n, w.vh, w.vl, w.t);
+    else rowdot_kernel<false><<<rows_grid, 256, 0, s>>>(O, m, n, w.vh, w.vl, w.t);
+    center_kernel<<<1, 1024, 0, s>>>(w.t, m, 1.0 / (double)m, w.scal + 1, w.wh, w.wl);
+    const int V = vec ? 4 : 1;
+    dim3 grid((unsigned)((n / V + 127) / 128), (unsigned)nch);
+    if (vec) colsum_kernel<true, true><<<grid, 128, 0, s>>>(O, m, n, rpc, w.wh, w.wl, nullptr, w.part2);
+    else colsum_kernel<false, true><<<grid, 128, 0, s>>>(O, m, n, rpc, w.wh, w.wl, nullptr, w.part2);
+    ctx->launches += 3;
+}
+
+}  // namespace vmc
+
+using namespace vmc;
+
+int vmc_sr_moments_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m,
+                        double *Obar, double *Ebar, double *G, cudaStream_t s)
+{
+    SrWs w;
+    int rc = sr_workspace(ctx, m, &w);
+    if (rc) return rc;
+    launch_moments(ctx, O, E, m, w, Obar, Ebar, G, s);
+    return vmc_cuda_check(ctx, cudaGetLastError(), "sr moments");
+}
+
+int vmc_sr_matvec_impl(vmc_ctx *ctx, const float *O, int64_t m, const double *Obar,
+                       const double *v, double shift, double *out, cudaStream_t s)
+{
+    (void)Obar;   // Obar . v equals the mean of t = O v; see the file comment
+    SrWs w;
+    int rc = sr_workspace(ctx, m, &w);
+    if (rc) return rc;
+    const int64_t n = ctx->n, nch = nchunks_for(m);
+    const int g = (int)std::min<int64_t>((n + 255) / 256, 4 * ctx->sm_count);
+    split_kernel<<<g, 256, 0, s>>>(v, n, w.vh, w.vl);
+    launch_sv_partials(ctx, O, m, w, s);
+    reduce_chunks_kernel<<<g, 256, 0, s>>>(w.part2, (int)nch, n, 1.0, v, shift, out);
+    ctx->launches += 2;
+    return vmc_cuda_check(ctx, cudaGetLastError(), "sr matvec");
+}
+
+// scale-split kernel: (wh, wl) = split(w_b) with no centring
+__global__ void split_scaled_kernel(const double *__restrict__ w, int64_t m, float *wh, float *wl)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m; b += (int64_t)gridDim.x * blockDim.x)
+        split(w[b], wh[b], wl[b]);
+}
+
+int vmc_ot_vec_impl(vmc_ctx *ctx, const float *O, int64_t m, const double *wv, double *out, cudaStream_t s)
+{
+    SrWs w;
+    int rc = sr_workspace(ctx, m, &w);
+    if (rc) return rc;
+    const int64_t n = ctx->n, nch = nchunks_for(m);
+    const int64_t rpc = (m + nch - 1) / nch;
+    split_scaled_kernel<<<(unsigned)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, s>>>(wv, m, w.wh, w.wl);
+    const bool vec = vec_ok(O, n);
+    const int V = vec ? 4 : 1;
+    dim3 grid((unsigned)((n / V + 127) / 128), (unsigned)nch);
+    if (vec) colsum_kernel<true, true><<<grid, 128, 0, s>>>(O, m, n, rpc, w.wh, w.wl, nullptr, w.part2);
+    else colsum_kernel<false, true><<<grid, 128, 0, s>>>(O, m, n, rpc, w.wh, w.wl, nullptr, w.part2);
+    const int g = (int)std::min<int64_t>((n + 255) / 256, 4 * ctx->sm_count);
+    reduce_chunks_kernel<<<g, 256, 0, s>>>(w.part2, (int)nch, n, 1.0, nullptr, 0.0, out);
+    ctx->launches += 3;
+    return vmc_cuda_check(ctx, cudaGetLastError(), "ot_vec");
+}
+
+static void record_cg(vmc_ctx *ctx, const float *O, int64_t m, double shift, int iters, double *x,
+                      const SrWs &w, cudaStream_t s)
+{
+    const int64_t n = ctx->n, nch = nchunks_for(m);
+    const int np = (int)std::min<int64_t>((n + 255) / 256, NPART);
+    double *rr0 = w.scal + 3, *rr1 = w.scal + 4, *gg = w.scal + 2;
+    cg_init_kernel<<<np, 256, 0, s>>>(w.G, n, x, w.r, w.p, w.vh, w.vl, w.gg_part);
+    finalize_scalar_kernel<<<1, 32, 0, s>>>(w.gg_part, np, gg, rr0);
+    ctx->launches += 2;
+    for (int it = 0; it < iters; ++it) {
+        double *rr_old = (it & 1) ? rr1 : rr0;
+        double *rr_new = (it & 1) ? rr0 : rr1;
+        launch_sv_partials(ctx, O, m, w, s);
+        cg_q_kernel<<<np, 256, 0, s>>>(w.part2, (int)nch, n, shift, w.p, w.q, w.pq_part);
+        cg_update_kernel<<<np, 256, 0, s>>>(w.pq_part, np, rr_old, x, w.r, w.p, w.q, n, w.rr_part);
+        cg_dir_kernel<<<np, 256, 0, s>>>(w.rr_part, np, rr_old, rr_new, w.r, w.p, n, w.vh, w.vl);
+        ctx->launches += 3;
+    }
+    resid_kernel<<<1, 32, 0, s>>>((iters & 1) ? rr1 : rr0, gg, w.scal + 5);
+    ctx->launches += 1;
+}
+
+int vmc_sr_solve_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m, double shift,
+                      int iters, double *x, double *resid_out, cudaStream_t s)
+{
+    SrWs w;
+    int rc = sr_workspace(ctx, m, &w);
+    if (rc) return rc;
+    launch_moments(ctx, O, E, m, w, w.Obar, w.scal + 0, w.G, s);
+    rc = vmc_cuda_check(ctx, cudaGetLastError(), "sr moments");
+    if (rc) return rc;
+    const bool same = ctx->cg_exec && ctx->cg_key_ws == ctx->sr_ws && ctx->cg_key_O == O && ctx->cg_key_m == m && ctx->cg_key_iters == iters &&
+                      ctx->cg_key_shift == shift && ctx->cg_key_x == x;
+    if (!same) {
+        if (ctx->cg_exec) { cudaGraphExecDestroy(ctx->cg_exec); ctx->cg_exec = nullptr; }
+        cudaStream_t cap;
+        rc = vmc_cuda_check(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "capture stream");
+        if (rc) return rc;
+        cudaGraph_t g;
+        const int64_t saved = ctx->launches;
+        rc = vmc_cuda_check(ctx, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        if (rc) { cudaStreamDestroy(cap); return rc; }
+        record_cg(ctx, O, m, shift, iters, x, w, cap);
+        cudaError_t e = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "end capture");
+        e = cudaGraphInstantiate(&ctx->cg_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { ctx->cg_exec = nullptr; return vmc_cuda_check(ctx, e, "graph instantiate"); }
+        ctx->cg_key_O = O; ctx->cg_key_m = m; ctx->cg_key_iters = iters; ctx->cg_key_shift = shift; ctx->cg_key_x = x;
+        ctx->cg_key_ws = ctx->sr_ws;
+        ctx->cg_launches = ctx->launches - saved;
+        ctx->launches = saved;
+    }
+    rc = vmc_cuda_check(ctx, cudaGraphLaunch(ctx->cg_exec, s), "graph launch");
+    if (rc) return rc;
+    ctx->launches += ctx->cg_launches;
+    if (resid_out) {
+        rc = vmc_cuda_check(ctx, cudaMemcpyAsync(resid_out, w.scal + 5, sizeof(double), cudaMemcpyDeviceToHost, s), "resid copy");
+        if (rc) return rc;
+        rc = vmc_cuda_check(ctx, cudaStreamSynchronize(s), "sync");
+        if (rc) return rc;
+    }
+    return VMC_OK;
+}

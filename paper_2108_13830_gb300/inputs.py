@@ -170,3 +170,19 @@ def ragged_inputs(w: Workload, per_L: int | None = None, scale: float = 1.0):
         o += c.size
     return (np.concatenate(packed).astype(np.int8), np.asarray(offs, np.int64),
             np.asarray(Ls, np.int32), theta)
+
+
+def synthetic_O(m: int, n: int, rng: np.random.Generator, dtype=np.float32) -> np.ndarray:
+    """Seeded stand-in for a log-derivative matrix: columns with nonzero means
+    and scales spread over two decades, plus a shared low-rank component
+    (samples are correlated), stored in FP32 like the library's O."""
+    scale = np.exp(rng.uniform(np.log(0.05), np.log(5.0), n))
+    mean = rng.normal(0.0, 1.0, n)
+    lowrank = rng.normal(0.0, 1.0, (m, 4)) @ rng.normal(0.0, 0.3, (4, n))
+    O = mean + scale * rng.standard_normal((m, n)) + lowrank
+    return O.astype(dtype)
+
+
+def synthetic_E(m: int, rng: np.random.Generator) -> np.ndarray:
+    """Stand-in local energies around -0.5 per site of a 10x10 lattice."""
+    return -50.0 + 3.0 * rng.standard_normal(m)

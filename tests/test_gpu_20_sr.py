@@ -1,0 +1,89 @@
+"""SR on the GPU (moments, S v, O^T w, CG) against the FP64 oracle on seeded
+synthetic O matrices (FP32 storage, as the library keeps O)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2108_13830_gb300 import inputs
+from paper_2108_13830_gb300.binding import VMC
+from gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+# (m, n, C, D): n must equal the context's parameter count
+CASES = [(256, 336, 4, 2), (4096, 14080, 16, 6)]
+
+
+def _ctx(C, D):
+    v = VMC(10, 1.0, 0.5, C, D, "fp32")
+    return v
+
+
+@pytest.fixture(scope="module", params=CASES, ids=lambda c: f"m{c[0]}n{c[1]}")
+def case(request):
+    m, n, C, D = request.param
+    rng = inputs.rng_for(40, m)
+    O = inputs.synthetic_O(m, n, rng)
+    E = inputs.synthetic_E(m, rng)
+    v = _ctx(C, D)
+    assert v.n == n
+    return O, E, v
+
+
+def test_moments(case):
+    O, E, v = case
+    ob, eb, g = v.sr_moments(to_dev(O), to_dev(E))
+    rob, reb, rg = oracle.sr_moments(O.astype(np.float64), E)
+    np.testing.assert_allclose(ob.cpu().numpy(), rob, rtol=1e-12, atol=1e-13)
+    assert abs(eb.item() - reb) <= 1e-13 * abs(reb)
+    np.testing.assert_allclose(g.cpu().numpy(), rg, rtol=1e-10, atol=1e-12 * np.abs(rg).max())
+
+
+def test_matvec(case):
+    O, E, v = case
+    Od = to_dev(O)
+    ob, _, _ = v.sr_moments(Od, to_dev(E))
+    rob, _, _ = oracle.sr_moments(O.astype(np.float64), E)
+    rng = np.random.default_rng(3)
+    for shift in (0.0, 1e-4):
+        x = rng.standard_normal(O.shape[1])
+        got = v.sr_matvec(Od, ob, to_dev(x), shift).cpu().numpy()
+        ref = oracle.sr_matvec(O.astype(np.float64), rob, x, shift)
+        np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-11 * np.abs(ref).max())
+
+
+def test_ot_vec(case):
+    O, E, v = case
+    w = np.random.default_rng(4).standard_normal(O.shape[0])
+    got = v.ot_vec(to_dev(O), to_dev(w)).cpu().numpy()
+    ref = O.astype(np.float64).T @ w
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
+
+
+def test_cg_matches_oracle(case):
+    O, E, v = case
+    x, res = v.sr_solve(to_dev(O), to_dev(E), shift=1e-4, iters=50)
+    rx, rres = oracle.sr_cg(O.astype(np.float64), E, 1e-4, 50)
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x - rx) <= 1e-7 * np.linalg.norm(rx)
+    assert abs(res - rres) <= 1e-6 * max(rres, 1e-30) + 1e-12
+
+
+def test_cg_replay_is_bitwise_stable(case):
+    O, E, v = case
+    Od, Ed = to_dev(O), to_dev(E)
+    out = torch.empty(O.shape[1], dtype=torch.float64, device="cuda")
+    x1, r1 = v.sr_solve(Od, Ed, 1e-4, 50, out=out)
+    a = x1.clone()
+    x2, r2 = v.sr_solve(Od, Ed, 1e-4, 50, out=out)
+    assert torch.equal(a, x2) and r1 == r2
+
+
+def test_single_sample_gives_zero():
+    v = _ctx(4, 2)
+    rng = inputs.rng_for(41)
+    O = inputs.synthetic_O(1, v.n, rng)
+    E = inputs.synthetic_E(1, rng)
+    x, res = v.sr_solve(to_dev(O), to_dev(E), 1e-4, 50)
+    assert torch.count_nonzero(x).item() == 0 and res == 0.0

@@ -1,0 +1,138 @@
+"""Parity of the tensor-core (tcgen05 BF16) path with the FP64 oracle at small
+sizes, plus checks that hold exactly: the constant-psi closed form,
+translation invariance, ragged vs uniform launches, and the bounded-wait
+timeout path."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2108_13830_gb300 import inputs
+from paper_2108_13830_gb300.binding import VMC, VMC_OK, VMC_ERR_TIMEOUT
+from gpu_util import bond_counts, make_ctx, to_dev
+
+pytestmark = pytest.mark.gpu
+
+BF16_TOL = 5e-4     # |E_gpu - E_oracle| / N per sample
+
+
+def _small(L, C, D, B, seed, kind="uniform", scale=1.0):
+    w = inputs.Workload(f"t{L}", L, C, D, "bf16", B, kind=kind, index=50 + seed)
+    sig, theta = inputs.workload_inputs(w, scale=scale)
+    return w, sig, theta
+
+
+@pytest.mark.parametrize("L,C,D,B", [(8, 32, 3, 48), (10, 16, 6, 48), (12, 32, 2, 24), (4, 16, 2, 64)])
+def test_bf16_local_energy_small(L, C, D, B):
+    w, sig, theta = _small(L, C, D, B, L + C)
+    v = make_ctx(w, theta=theta)
+    e, nn = v.local_energy(to_dev(sig))
+    assert v.sync_status()[0] == VMC_OK
+    e = e.cpu().numpy()
+    a1, a2 = bond_counts(sig)
+    np.testing.assert_array_equal(nn.cpu().numpy(), a1 + a2)
+    re, _ = oracle.local_energy(L, w.J1, w.J2, C, D, theta, sig)
+    err = np.abs(e - re) / (L * L)
+    assert err.max() <= BF16_TOL, err.max()
+
+
+def test_bf16_logpsi_small():
+    w, sig, theta = _small(8, 32, 3, 64, 7)
+    v = make_ctx(w, theta=theta)
+    la, sg = v.logpsi(to_dev(sig))
+    ra, rs = oracle.logpsi(w.L, w.C, w.D, theta, sig)
+    np.testing.assert_array_equal(sg.cpu().numpy().astype(np.int32), rs)
+    # BF16 activations: log|psi| is a sum of C N log terms, each off by ~1e-3 relative
+    assert np.abs(la.cpu().numpy() - ra).max() <= 0.05 + 1e-3 * np.abs(ra).max()
+
+
+@pytest.mark.parametrize("L", [6, 8, 16])
+def test_bf16_constant_psi_closed_form(L):
+    """All weights zero and last bias 1: psi = 1 exactly in BF16, so E_loc is
+    the integer closed form (J1/4)(P1-A1) + (J2/4)(P2-A2) - (J1/2)A1 + (J2/2)A2."""
+    C, D = 32, 2
+    w = inputs.Workload("c", L, C, D, "bf16", 32)
+    theta = np.zeros(inputs.num_params(C, D))
+    ow, ob = inputs.param_offsets(C, D)[-1]
+    theta[ob:ob + C] = 1.0
+    sig = inputs.uniform_configs(L, 32, inputs.rng_for(60 + L))
+    v = make_ctx(w, theta=theta)
+    e, nn = v.local_energy(to_dev(sig))
+    a1, a2 = bond_counts(sig)
+    N2 = 2 * L * L
+    closed = 0.25 * (N2 - 2 * a1) + 0.125 * (N2 - 2 * a2) - 0.5 * a1 + 0.25 * a2
+    np.testing.assert_array_equal(e.cpu().numpy(), closed)
+
+
+def test_bf16_translation_invariance():
+    w, sig, theta = _small(10, 16, 4, 16, 9)
+    v = make_ctx(w, theta=theta)
+    la, _ = v.logpsi(to_dev(sig))
+    e, _ = v.local_energy(to_dev(sig))
+    sh = np.ascontiguousarray(np.roll(np.roll(sig, 3, axis=1), -2, axis=2))
+    la2, _ = v.logpsi(to_dev(sh))
+    e2, _ = v.local_energy(to_dev(sh))
+    # every z is bitwise the same per cell; only the order of the FP64 sums moves
+    np.testing.assert_allclose(la2.cpu().numpy(), la.cpu().numpy(), rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(e2.cpu().numpy(), e.cpu().numpy(), rtol=1e-9, atol=1e-9)
+
+
+def test_bf16_ragged_equals_uniform_and_oracle():
+    w = inputs.WORKLOADS["ragged_8_16"]
+    packed, offs, Ls, theta = inputs.ragged_inputs(w, per_L=6)
+    v = make_ctx(w, theta=theta, L=16)
+    e, nn = v.local_energy_ragged(to_dev(packed), to_dev(offs), to_dev(Ls), 16)
+    assert v.sync_status()[0] == VMC_OK
+    e = e.cpu().numpy()
+    for L in w.Ls:
+        idx = np.where(Ls == L)[0]
+        cfg = np.stack([packed[offs[b]:offs[b] + L * L].reshape(L, L) for b in idx])
+        vu = make_ctx(w, theta=theta, L=L)
+        eu, _ = vu.local_energy(to_dev(cfg))
+        np.testing.assert_allclose(e[idx], eu.cpu().numpy(), rtol=1e-12, atol=1e-10)
+        re, rn = oracle.local_energy(L, w.J1, w.J2, w.C, w.D, theta, cfg[:2])
+        assert (np.abs(e[idx[:2]] - re) / (L * L)).max() <= BF16_TOL
+        np.testing.assert_array_equal(nn.cpu().numpy()[idx[:2]], rn)
+
+
+@pytest.mark.parametrize("G,S", [(1, 1), (1, 2), (3, 2), (2, 1)])
+def test_bf16_tile_choices_agree(G, S):
+    """Every slab geometry gives bitwise the same energies (rows are independent)."""
+    w, sig, theta = _small(8, 32, 3, 40, 11)
+    v = make_ctx(w, theta=theta)
+    ref, _ = v.local_energy(to_dev(sig))
+    v.set_tiles(8, slab_configs=G, slabs=S)
+    got, _ = v.local_energy(to_dev(sig))
+    assert torch.equal(ref, got)
+
+
+def test_bf16_autotune_keeps_results():
+    w, sig, theta = _small(8, 32, 3, 40, 12)
+    v = make_ctx(w, theta=theta)
+    ref, _ = v.local_energy(to_dev(sig))
+    tiles = v.autotune(8, probe_B=64)
+    assert tiles["slab_configs"] >= 1
+    got, _ = v.local_energy(to_dev(sig))
+    assert torch.equal(ref, got)
+
+
+def test_wait_timeout_reports_status():
+    w, sig, theta = _small(8, 32, 3, 8, 13)
+    v = make_ctx(w, theta=theta)
+    v.debug_wait_timeout(2_000_000)          # 2 ms on a barrier nothing arrives on
+    rc, _ = v.sync_status()
+    assert rc == VMC_ERR_TIMEOUT
+    e, _ = v.local_energy(to_dev(sig))       # the context stays usable
+    assert v.sync_status()[0] == VMC_OK
+    assert np.all(np.isfinite(e.cpu().numpy()))
+
+
+def test_nonfinite_parameters_are_flagged():
+    w, sig, theta = _small(8, 32, 3, 8, 14)
+    th = theta.copy()
+    th[5] = np.nan
+    v = make_ctx(w, theta=th)
+    e, _ = v.local_energy(to_dev(sig))
+    rc, nf = v.sync_status()
+    assert rc == -3 and nf == 8
+    assert np.all(np.isnan(e.cpu().numpy()))
