@@ -56,13 +56,18 @@ __device__ __forceinline__ void load_w(const T *__restrict__ w, T (&out)[CO])
 // One 3x3 circular convolution layer over `nconf` configurations.
 // in: shared, [nconf][cin][PP] padded planes (conf stride in_cs elements).
 // Work item = (conf, output-channel block, row y, pixel pair x0): CO x 2
-// accumulators, bias first, then ci, ky, kx in order.  epi(it, conf, c0, y,
-// x0, acc) consumes the result; items are numbered conf-major.
+// outputs.  FP64: one FMA chain (bias, then ci, ky, kx in order).  FP32:
+// for each input channel the nine taps form a short FMA chain, and the
+// per-channel partial sums are added with Kahan compensation (Kahan 1965),
+// so the rounding of a K = 9 c_in term sum stays at the level of a single
+// FP32 rounding instead of growing with sqrt(K).  epi(it, conf, c0, y, x0,
+// acc) consumes the result; items are numbered conf-major.
 template <typename T, int CO, class Epi>
 __device__ __forceinline__ void conv_layer(const T *__restrict__ in, int in_cs, int cin,
                                            const T *__restrict__ W, const T *__restrict__ bias,
                                            int cout, int L, int PP, int nconf, Epi epi)
 {
+    constexpr bool KAHAN = (sizeof(T) == 4);
     const int LP = L + 2, hx = L >> 1;
     const int nblk = cout / CO;
     const int per_row = hx, per_blk = L * hx, per_conf = nblk * per_blk;
@@ -74,16 +79,24 @@ __device__ __forceinline__ void conv_layer(const T *__restrict__ in, int in_cs, 
         r -= cb * per_blk;
         const int y = r / per_row;
         const int x0 = (r - y * per_row) * 2;
-        T acc[CO][2];
+        T acc[CO][2], comp[CO][2];
 #pragma unroll
         for (int co = 0; co < CO; ++co) {
             const T bv = bias ? bias[cb * CO + co] : T(0);
             acc[co][0] = bv;
             acc[co][1] = bv;
+            comp[co][0] = T(0);
+            comp[co][1] = T(0);
         }
         const T *ip = in + conf * in_cs + y * LP + x0;
         const T *wp = W + (size_t)cb * cin * 9 * CO;
         for (int ci = 0; ci < cin; ++ci) {
+            T part[CO][2];
+#pragma unroll
+            for (int co = 0; co < CO; ++co) {
+                part[co][0] = KAHAN ? T(0) : acc[co][0];
+                part[co][1] = KAHAN ? T(0) : acc[co][1];
+            }
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky) {
                 const T *rp = ip + ci * PP + ky * LP;
@@ -96,10 +109,30 @@ __device__ __forceinline__ void conv_layer(const T *__restrict__ in, int in_cs, 
                     const T i1 = (kx == 0) ? a1 : ((kx == 1) ? a2 : a3);
 #pragma unroll
                     for (int co = 0; co < CO; ++co) {
-                        acc[co][0] = fma(w[co], i0, acc[co][0]);
-                        acc[co][1] = fma(w[co], i1, acc[co][1]);
+                        part[co][0] = fma(w[co], i0, part[co][0]);
+                        part[co][1] = fma(w[co], i1, part[co][1]);
                     }
                 }
+            }
+#pragma unroll
+            for (int co = 0; co < CO; ++co)
+#pragma unroll
+                for (int px = 0; px < 2; ++px) {
+                    if constexpr (KAHAN) {
+                        const T yk = part[co][px] - comp[co][px];
+                        const T tk = acc[co][px] + yk;
+                        comp[co][px] = (tk - acc[co][px]) - yk;
+                        acc[co][px] = tk;
+                    } else {
+                        acc[co][px] = part[co][px];
+                    }
+                }
+        }
+        if constexpr (KAHAN) {
+#pragma unroll
+            for (int co = 0; co < CO; ++co) {
+                acc[co][0] -= comp[co][0];
+                acc[co][1] -= comp[co][1];
             }
         }
         epi(it, conf, cb * CO, y, x0, acc);

@@ -84,7 +84,7 @@ struct Ctrl {
     int action, ok;
     long long new_b;
     int new_L;
-    int cur_parent, cur_k, cur_nlist;
+    int cur_parent, cur_k, cur_nlist, cur_L;
     long long pending_b;
     int no_more, ring_head;
     int seg_first, seg_n;
@@ -483,7 +483,7 @@ struct Kern {
                     const int r = c.ring_head;
                     c.ring_head = (r + 1) % RING;
                     Parent &P = c.ring[r];
-                    if (P.valid) c.abort = 1;   // cannot happen with RING >= 2 * MAX_SLOTS + 2
+                    if (P.valid) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); }   // cannot happen: RING > parents in flight
                     P.b = b;
                     P.diag = (p.mode == 1) ? diag_energy(Lb, c.nb_a1, c.nb_a2, p.J1, p.J2) : 0.0;
                     P.la0 = 0.0; P.acc = 0.0; P.sg0 = 0;
@@ -495,16 +495,21 @@ struct Kern {
                     c.cur_parent = r;
                     c.cur_k = 0;
                     c.cur_nlist = c.nb_cnt;
-                    if (m.count == 0) {
-                        m.L = Lb;
-                        m.G = p.geo[Lb >> 1].G;
-                        m.T = p.geo[Lb >> 1].T;
-                        m.PW = p.geo[Lb >> 1].PW;
-                    }
+                    c.cur_L = Lb;
                 }
                 epi_sync();
             }
             if (tid == 0) {
+                if (m.count == 0) {
+                    // the slab takes the geometry of the lattice now at the cursor
+                    // (a new parent, or the rest of the previous fill's parent)
+                    const int Lc = c.cur_L;
+                    m.L = Lc;
+                    m.G = p.geo[Lc >> 1].G;
+                    m.T = p.geo[Lc >> 1].T;
+                    m.PW = p.geo[Lc >> 1].PW;
+                }
+                if (m.G < 1 || m.G > MAX_SLOTS) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); m.G = 1; }
                 const int n_take = min(m.G - m.count, c.cur_nlist + 1 - c.cur_k);
                 for (int i = 0; i < n_take; ++i) {
                     const int kk = c.cur_k + i;
@@ -599,7 +604,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
         }
         mbar_init(&c.drain, 1);
         c.abort = 0;
-        c.cur_parent = -1; c.cur_k = 0; c.cur_nlist = -1;
+        c.cur_parent = -1; c.cur_k = 0; c.cur_nlist = -1; c.cur_L = 0;
+        for (int i = 0; i < 2; ++i) { c.slab[i].count = 0; c.slab[i].L = 0; c.slab[i].G = 0; c.slab[i].T = 0; c.slab[i].PW = 0; }
         c.pending_b = -1; c.no_more = 0; c.ring_head = 0;
         for (int r = 0; r < RING; ++r) c.ring[r].valid = 0;
         mbar_fence_init();

@@ -246,6 +246,7 @@ int vmc_sync_status(vmc_ctx *ctx, void *stream, int64_t *nonfinite)
     if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "status read");
     if (nonfinite) *nonfinite = (int64_t)st.nonfinite;
     if (st.flags & VMC_STATUS_TIMEOUT) return vmc_fail(ctx, VMC_ERR_TIMEOUT, "device wait timed out (site %d)", st.timeout_site);
+    if (st.flags & VMC_STATUS_INTERNAL) return vmc_fail(ctx, VMC_ERR_STATE, "internal scheduling error in the persistent kernel");
     if (st.flags & VMC_STATUS_BADARG) return vmc_fail(ctx, VMC_ERR_ARG, "a sample had an invalid lattice size");
     if (st.flags & VMC_STATUS_NONFINITE) return vmc_fail(ctx, VMC_ERR_NONFINITE, "%llu samples non-finite", st.nonfinite);
     return VMC_OK;

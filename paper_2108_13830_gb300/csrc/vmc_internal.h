@@ -18,6 +18,7 @@ struct DevStatus {
 #define VMC_STATUS_NONFINITE 1
 #define VMC_STATUS_TIMEOUT 2
 #define VMC_STATUS_BADARG 4
+#define VMC_STATUS_INTERNAL 8
 
 // Everything a forward / local-energy kernel needs to know about the model.
 struct NetDesc {

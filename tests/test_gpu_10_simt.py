@@ -52,22 +52,28 @@ def test_fp64_log_derivs_vs_oracle(l4):
 
 
 def test_fp64_log_derivs_vs_finite_differences(l4):
-    """O_k against central differences of the GPU log|psi| (FP64)."""
+    """O_k against Richardson-extrapolated central differences of the GPU
+    log|psi| (FP64): D(h) = (f(x+h) - f(x-h)) / 2h, (4 D(h/2) - D(h)) / 3
+    has an O(h^4) truncation error."""
     w, sig, theta, v = l4
     s = to_dev(sig[:2])
     O = v.log_derivs(s, dtype=torch.float64).cpu().numpy()
-    fd = np.zeros_like(O)
-    for k in range(theta.size):
-        h = 1e-5 * max(1.0, abs(theta[k]))
+
+    def central(k, h):
         tp = theta.copy(); tp[k] += h
         tm = theta.copy(); tm[k] -= h
         v.set_params(to_dev(tp))
         lp, _ = v.logpsi(s)
         v.set_params(to_dev(tm))
         lm, _ = v.logpsi(s)
-        fd[:, k] = ((lp - lm) / (2 * h)).cpu().numpy()
+        return ((lp - lm) / (2 * h)).cpu().numpy()
+
+    fd = np.zeros_like(O)
+    for k in range(theta.size):
+        h = 1e-4 * max(1.0, abs(theta[k]))
+        fd[:, k] = (4 * central(k, h / 2) - central(k, h)) / 3
     v.set_params(to_dev(theta))
-    np.testing.assert_allclose(O, fd, rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(O, fd, rtol=1e-6, atol=1e-8 * np.abs(O).max())
 
 
 def test_autograd_backward(l4):
@@ -79,8 +85,11 @@ def test_autograd_backward(l4):
     gw = torch.linspace(-1.0, 1.0, 32, dtype=torch.float64, device="cuda")
     (la * gw).sum().backward()
     R = oracle.log_derivs(w.L, w.C, w.D, theta, sig[:32])
-    ref = R.T @ gw.cpu().numpy()
-    np.testing.assert_allclose(th.grad.cpu().numpy(), ref, rtol=1e-9, atol=1e-9)
+    g = gw.cpu().numpy()
+    ref = R.T @ g
+    # the backward stores O in FP32 (unit roundoff 2^-24) before O^T grad
+    bound = 2.0 ** -23 * (np.abs(R).T @ np.abs(g))
+    assert np.all(np.abs(th.grad.cpu().numpy() - ref) <= bound + 1e-15)
 
 
 @pytest.fixture(scope="module")

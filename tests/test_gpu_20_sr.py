@@ -37,7 +37,12 @@ def test_moments(case):
     rob, reb, rg = oracle.sr_moments(O.astype(np.float64), E)
     np.testing.assert_allclose(ob.cpu().numpy(), rob, rtol=1e-12, atol=1e-13)
     assert abs(eb.item() - reb) <= 1e-13 * abs(reb)
-    np.testing.assert_allclose(g.cpu().numpy(), rg, rtol=1e-10, atol=1e-12 * np.abs(rg).max())
+    # The oracle follows Eq. 5 literally, G = <O E> - <E><O>, which cancels
+    # when |<E>| >> std(E); its FP64 error is bounded by ~m eps (<|O E|> +
+    # |<E><O>|).  The GPU sums the centred form with double-float accuracy.
+    Od = O.astype(np.float64)
+    bound = 4 * O.shape[0] * np.finfo(np.float64).eps * (np.abs(Od * E[:, None]).mean(axis=0) + np.abs(reb * rob))
+    assert np.all(np.abs(g.cpu().numpy() - rg) <= bound)
 
 
 def test_matvec(case):
@@ -61,13 +66,33 @@ def test_ot_vec(case):
     np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
 
 
-def test_cg_matches_oracle(case):
+def test_cg_matches_oracle_well_conditioned(case):
+    """With shift 1 the system is well conditioned: 50 CG steps of the GPU
+    and of the oracle agree to ~1e-9 (two FP64 CGs differ by their rounding)."""
     O, E, v = case
-    x, res = v.sr_solve(to_dev(O), to_dev(E), shift=1e-4, iters=50)
-    rx, rres = oracle.sr_cg(O.astype(np.float64), E, 1e-4, 50)
+    x, res = v.sr_solve(to_dev(O), to_dev(E), shift=1.0, iters=50)
+    rx, rres = oracle.sr_cg(O.astype(np.float64), E, 1.0, 50)
     x = x.cpu().numpy()
-    assert np.linalg.norm(x - rx) <= 1e-7 * np.linalg.norm(rx)
-    assert abs(res - rres) <= 1e-6 * max(rres, 1e-30) + 1e-12
+    assert np.linalg.norm(x - rx) <= 1e-8 * np.linalg.norm(rx)
+
+
+def test_cg_residual_quality_at_small_shift(case):
+    """Shift 1e-4 (the workload's): after 50 unconverged steps two FP64 CG
+    runs differ at the 1e-3 level by rounding alone (kappa ~ 1e5-1e6), so the
+    check is on what CG guarantees: the true residual of the GPU's x,
+    measured with the oracle's matvec, matches the oracle CG's residual, and
+    the GPU's reported residual is that true residual."""
+    O, E, v = case
+    shift = 1e-4
+    x, res = v.sr_solve(to_dev(O), to_dev(E), shift=shift, iters=50)
+    rx, rres = oracle.sr_cg(O.astype(np.float64), E, shift, 50)
+    Od = O.astype(np.float64)
+    ob, _, g = oracle.sr_moments(Od, E)
+    x = x.cpu().numpy()
+    true_res = np.linalg.norm(g - oracle.sr_matvec(Od, ob, x, shift)) / np.linalg.norm(g)
+    assert true_res <= 1.5 * rres + 1e-12
+    assert abs(res - true_res) <= 0.05 * true_res + 1e-12
+    assert np.linalg.norm(x - rx) <= 0.1 * np.linalg.norm(rx)
 
 
 def test_cg_replay_is_bitwise_stable(case):
