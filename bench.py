@@ -1,0 +1,407 @@
+"""Throughput benchmark of the CNN-VMC hot path on GB300.
+
+One step = the whole hot path on one batch of seeded synthetic samples:
+local energies E_loc (every J1/J2 exchange neighbour through the BF16
+tensor-core CNN), per-sample log-derivatives O_k, SR moments and the
+matrix-free CG solve of (S + shift I) x = G.  Metric: samples per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+
+Multi-GPU (torchrun): every rank runs its own batch (weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and
+the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2108_13830_gb300 import inputs  # noqa: E402
+
+METRIC = "E_loc+O_k samples/sec at L=16,24 (BF16-TC vs FP32 plain); roofline %"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def f_fwd(L, C, D):
+    """Algorithmic FLOPs of one forward pass: 2 N (9 C + 9 D C^2)."""
+    return 2.0 * L * L * (9 * C + 9 * D * C * C)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(FALLBACK_PEAKS), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(w, budget_s=20.0):
+    """Oracle (FP64, plain C, OpenMP over configurations) samples/s on a
+    bounded sample of the workload: log|psi| of the first neighbours of
+    sample 0 (all cores), O_k of a few samples (all cores) and one S v on a
+    row subsample; the per-sample cost is assembled from the exact neighbour
+    counts of the batch and the 50 + 1 S v passes of the solve."""
+    import oracle
+    sig, theta = inputs.workload_inputs(w, batch=64)
+    nthreads = oracle.max_threads()
+    L, C, D = w.L, w.C, w.D
+    # neighbour configurations of sample 0 (the oracle's own bond rule)
+    s0 = sig[0]
+    nbrs = []
+    for y in range(L):
+        for x in range(L):
+            for dy, dx in ((0, 1), (1, 0), (1, 1), (1, -1)):
+                y2, x2 = (y + dy) % L, (x + dx) % L
+                if s0[y, x] != s0[y2, x2]:
+                    t = s0.copy()
+                    t[y, x], t[y2, x2] = s0[y2, x2], s0[y, x]
+                    nbrs.append(t)
+    n_avg = float(np.mean([len(nbrs)]))
+    # timing probes, growing until ~budget/3 each
+    k = max(nthreads, 1)
+    t0 = time.perf_counter()
+    oracle.logpsi(L, C, D, theta, np.stack(nbrs[:k]), nthreads=nthreads)
+    t_lp = (time.perf_counter() - t0) / k
+    kd = max(1, min(nthreads, 16))
+    t0 = time.perf_counter()
+    oracle.log_derivs(L, C, D, theta, sig[:kd], nthreads=nthreads)
+    t_ld = (time.perf_counter() - t0) / kd
+    n = inputs.num_params(C, D)
+    m_sub = 64
+    rng = inputs.rng_for(99)
+    Osub = inputs.synthetic_O(m_sub, n, rng).astype(np.float64)
+    ob = Osub.mean(axis=0)
+    v = rng.standard_normal(n)
+    t0 = time.perf_counter()
+    oracle.sr_matvec(Osub, ob, v, 1e-4)
+    t_mv_row = (time.perf_counter() - t0) / m_sub          # per row of O, one S v
+    per_sample = (1.0 + n_avg) * t_lp + t_ld + (w.cg_iters + 1) * t_mv_row
+    sample = (f"log|psi| of {k} exchange neighbours of one {L}x{L} sample, O_k of {kd} samples "
+              f"(OpenMP, {nthreads} threads) and one S v over {m_sub} synthetic O rows; per-sample "
+              f"cost = (1 + {n_avg:.0f} neighbours) t_logpsi + t_O + {w.cg_iters + 1} t_Sv/row")
+    return 1.0 / per_sample, nthreads, sample
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    rates = []
+    sample = ""
+    cores = 1
+    for i in range(args.warmup + args.steps):
+        r, cores, sample = cpu_oracle_rate(w)
+        if i >= args.warmup:
+            rates.append(r)
+    value = float(np.median(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.batch / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "L": w.L, "C": w.C, "D": w.D, "batch": w.batch},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": "samples/s", "cores": cores,
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="L24_bf16_sr", choices=sorted(inputs.WORKLOADS))
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-also", action="store_true", help="skip the L=16 / FP32 side measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--eloc-only", action="store_true",
+                    help="profiling case: only the local-energy launch, no JSON contract line")
+    ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
+    ap.add_argument("--precision", default="", help="override the tensor-core operand type (bf16 | fp16)")
+    args = ap.parse_args()
+    w = inputs.WORKLOADS[args.workload]
+    if args.batch:
+        import dataclasses
+        w = dataclasses.replace(w, batch=args.batch)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    from paper_2108_13830_gb300.binding import VMC
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    peaks, peak_src = load_peaks()
+    B, L, C, D = w.batch, w.L, w.C, w.D
+    sig, theta = inputs.workload_inputs(w)
+    prec = args.precision or ("bf16" if w.precision in ("bf16", "fp32") else w.precision)
+    if args.eloc_only:
+        return eloc_only(args, w, sig, theta, prec)
+    ctx = VMC(L, w.J1, w.J2, C, D, prec)
+    ctx.set_params(torch.tensor(theta, device="cuda"))
+    s_dev = torch.tensor(sig, device="cuda")
+    eloc = torch.empty(B, dtype=torch.float64, device="cuda")
+    nnb = None
+    O = torch.empty(B, ctx.n, dtype=torch.float32, device="cuda")
+    x = torch.empty(ctx.n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    # exact neighbour counts for the algorithmic FLOPs of the E_loc launch
+    _, nnb = ctx.local_energy(s_dev)
+    n_configs = int(B + nnb.sum().item())
+    flops_eloc = n_configs * f_fwd(L, C, D)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(times):
+        e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+        e0.record(stream)
+        ctx.local_energy(s_dev, out=eloc, n_nbr=False)
+        nl = ctx.last_launch_count
+        e1.record(stream)
+        ctx.log_derivs(s_dev, out=O)
+        nl += ctx.last_launch_count
+        e2.record(stream)
+        ctx.sr_solve(O, eloc, w.shift, w.cg_iters, out=x, resid=False)
+        nl += ctx.last_launch_count
+        e3.record(stream)
+        times.append((e0, e1, e2, e3))
+        return nl
+
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, launches = [], 0
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()                      # L2 flush, outside the step's event pair
+        launches += step(times)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(d) for a, b, c, d in times]
+    eloc_ms = [a.elapsed_time(b) for a, b, c, d in times]
+    od_ms = [b.elapsed_time(c) for a, b, c, d in times]
+    sr_ms = [c.elapsed_time(d) for a, b, c, d in times]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API with host buffers
+    sig_host = torch.tensor(sig).pin_memory()
+    eloc_host = torch.empty(B, dtype=torch.float64).pin_memory()
+    x_host = torch.empty(ctx.n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(max(2, args.steps // 2) + 1):
+        flush.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        s_dev.copy_(sig_host, non_blocking=True)
+        ctx.local_energy(s_dev, out=eloc, n_nbr=False)
+        ctx.log_derivs(s_dev, out=O)
+        ctx.sr_solve(O, eloc, w.shift, w.cg_iters, out=x, resid=False)
+        eloc_host.copy_(eloc, non_blocking=True)
+        x_host.copy_(x, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e_value = world * B / (statistics.mean(e2e_ms) / 1e3)
+
+    peak_t = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    eloc_mean = statistics.mean(eloc_ms)
+    achieved = flops_eloc / (eloc_mean / 1e3) / 1e12
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        try:
+            traffic = json.load(open(tp)).get(f"tc_eloc_{w.name}")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
+                "frac": achieved / peak_t, "traffic": traffic, "kernel": "tc_eloc_kernel<32>",
+                "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "algorithmic_flops_per_launch": flops_eloc, "configs_per_launch": n_configs,
+                "launch_ms": eloc_mean}
+    sr_mean = statistics.mean(sr_ms)
+    hbm = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
+    sr_bytes = (w.cg_iters + 1) * B * ctx.n * 4
+    roofline_sr = {"bound": "hbm", "achieved": sr_bytes / (sr_mean / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                   "frac": sr_bytes / (sr_mean / 1e3) / 1e9 / hbm,
+                   "algorithmic_bytes": sr_bytes, "note": "one read of O per S v (51 passes incl. moments)"}
+
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": prec, "data": "synthetic",
+            "config": {"workload": w.name, "L": L, "C": C, "D": D, "batch": B, "params": ctx.n,
+                       "neighbours_per_sample": (n_configs - B) / B, "sr_shift": w.shift,
+                       "cg_iters": w.cg_iters, "parallelism": f"replicas x{world}",
+                       "l2": "flushed before each step (256 MiB write outside the step's events)"},
+            "breakdown_ms": {"eloc": eloc_mean, "log_derivs": statistics.mean(od_ms), "sr_solve": sr_mean},
+            "roofline": roofline, "roofline_sr": roofline_sr,
+            "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(sig_host.numel()),
+                    "d2h_bytes_per_step": int(8 * B + 8 * ctx.n)},
+            "gpu_launches": int(launches), "clocks": clk}
+
+    if not args.no_also and rank == 0:
+        line["also"] = side_measurements(torch, VMC, ev, stream)
+    if rank == 0 and not args.no_cpu:
+        try:
+            r, cores, sample = cpu_oracle_rate(w)
+            line["cpu_baseline"] = {"value": r, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                                    "sample": sample}
+        except Exception as e:  # report, never hide
+            line["cpu_baseline"] = {"value": None, "error": str(e)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def eloc_only(args, w, sig, theta, prec):
+    """Local-energy launches only, on `w.batch` samples (profiling cases)."""
+    import torch
+    from paper_2108_13830_gb300.binding import VMC
+    ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, prec)
+    ctx.set_params(torch.tensor(theta, device="cuda"))
+    s = torch.tensor(sig, device="cuda")
+    e = torch.empty(w.batch, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        ctx.local_energy(s, out=e, n_nbr=False)
+    rc, _ = ctx.sync_status()
+    print(json.dumps({"eloc_only": w.name, "batch": w.batch, "precision": prec, "status": rc}))
+    return 0 if rc == 0 else 1
+
+
+def side_measurements(torch, VMC, ev, stream):
+    """E_loc + O_k samples/s at L = 16 and L = 24 for the BF16 tensor-core and
+    the plain FP32 paths (FP32 on a sub-batch to bound the run time)."""
+    out = {}
+    for name, prec, B in (("L16_bf16", "bf16", 8192), ("L16_bf16", "fp32", 256),
+                          ("L24_bf16_sr", "bf16", 4096), ("L24_bf16_sr", "fp32", 64)):
+        w = inputs.WORKLOADS[name]
+        sig, theta = inputs.workload_inputs(w, batch=B)
+        ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, prec)
+        ctx.set_params(torch.tensor(theta, device="cuda"))
+        s = torch.tensor(sig, device="cuda")
+        e = torch.empty(B, dtype=torch.float64, device="cuda")
+        O = torch.empty(B, ctx.n, dtype=torch.float32, device="cuda")
+        _, nn = ctx.local_energy(s)
+        ncfg = int(B + nn.sum().item())
+        ctx.log_derivs(s, out=O)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(2):
+            a, b, c = ev(), ev(), ev()
+            a.record(stream)
+            ctx.local_energy(s, out=e, n_nbr=False)
+            b.record(stream)
+            ctx.log_derivs(s, out=O)
+            c.record(stream)
+            torch.cuda.synchronize()
+            ts.append((a.elapsed_time(b), b.elapsed_time(c)))
+        te = min(t[0] for t in ts)
+        to = min(t[1] for t in ts)
+        out[f"L{w.L}_{prec}"] = {"samples_per_s": B / ((te + to) / 1e3), "batch": B,
+                                 "eloc_ms": te, "log_derivs_ms": to,
+                                 "eloc_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (te / 1e3) / 1e12}
+        ctx.close()
+        del O
+        torch.cuda.empty_cache()
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

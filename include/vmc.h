@@ -51,18 +51,20 @@ extern "C" {
 
 /* Arithmetic of the convolutions.  VMC_BF16 runs the C -> C and embedding
  * convolutions on tcgen05 tensor cores with BF16 operands and FP32
- * accumulation; log|psi| sums, amplitude ratios and E_loc sums are FP64 in
- * every precision. */
+ * accumulation; VMC_FP16 is the same tensor-core path with FP16 operands
+ * (same rate, 11-bit instead of 8-bit significands).  log|psi| sums,
+ * amplitude ratios and E_loc sums are FP64 in every precision. */
 #define VMC_FP64 0
 #define VMC_FP32 1
 #define VMC_BF16 2
+#define VMC_FP16 3
 
 typedef struct vmc_ctx vmc_ctx;
 
 typedef struct {
     int n_layers_cc;     /* D >= 1: number of C -> C layers after the 1 -> C embedding */
-    int channels;        /* C: 4..64, multiple of 4 (multiple of 16 for VMC_BF16) */
-    int precision;       /* VMC_FP64 | VMC_FP32 | VMC_BF16 */
+    int channels;        /* C: 4..64, multiple of 4 (16 or 32 for VMC_BF16 / VMC_FP16) */
+    int precision;       /* VMC_FP64 | VMC_FP32 | VMC_BF16 | VMC_FP16 */
     int marshall_sign;   /* 1: include (-1)^{M_A} (Eq. 9) in the sign and E_loc */
 } vmc_arch;
 
@@ -77,8 +79,7 @@ typedef struct {
 /* Create a context for L x L lattices with couplings J1, J2 (Eq. 3) and the
  * network `arch`.  Binds the current CUDA device.  *out receives the
  * context; on failure *out is NULL and the return code says why
- * (VMC_ERR_UNSUPPORTED when precision is VMC_BF16 and the device is not
- * sm_103). */
+ * (VMC_ERR_UNSUPPORTED when the device is not sm_103). */
 int vmc_create(int L, double J1, double J2, const vmc_arch *arch, vmc_ctx **out);
 void vmc_destroy(vmc_ctx *ctx);
 

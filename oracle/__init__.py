@@ -34,6 +34,8 @@ def lib():
         L.orc_logpsi_batch.argtypes = [_I, _I, _I, _dp, _I, _i8p, _I64, _dp, _i32p, _I]
         L.orc_local_energy_batch.argtypes = [_I, _D, _D, _I, _I, _dp, _I, _i8p, _I64, _dp,
                                              _ct.c_void_p, _I]
+        L.orc_local_energy_cnn_par.restype = _D
+        L.orc_local_energy_cnn_par.argtypes = [_I, _D, _D, _I, _I, _dp, _I, _i8p, _ct.c_void_p, _I]
         L.orc_local_energy_table.restype = _D
         L.orc_local_energy_table.argtypes = [_I, _D, _D, _dp, _i8p]
         L.orc_log_derivs_batch.argtypes = [_I, _I, _I, _dp, _i8p, _I64, _dp, _I]
@@ -87,6 +89,20 @@ def local_energy(L, J1, J2, C, D, theta, sigma, marshall=True, nthreads=0):
     nn = _np.zeros(B, _np.int32)
     lib().orc_local_energy_batch(L, J1, J2, C, D, _f64(theta), int(marshall), s, B, e,
                                  nn.ctypes.data, nthreads)
+    return e, nn
+
+
+def local_energy_par(L, J1, J2, C, D, theta, sigma, marshall=True, nthreads=0):
+    """Same as local_energy, one sample at a time with its neighbours spread
+    over threads (for large lattices)."""
+    s, B = _cfg(sigma, L)
+    e = _np.zeros(B)
+    nn = _np.zeros(B, _np.int32)
+    th = _f64(theta)
+    for b in range(B):
+        row = _np.ascontiguousarray(s[b])
+        e[b] = lib().orc_local_energy_cnn_par(L, J1, J2, C, D, th, int(marshall), row,
+                                              nn[b:].ctypes.data, nthreads)
     return e, nn
 
 

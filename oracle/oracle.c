@@ -228,6 +228,49 @@ void orc_local_energy_batch(int L, double J1, double J2, int C, int D, const dou
                                        n_nbr ? n_nbr + b : NULL);
 }
 
+/* E_loc of one sample with the neighbour evaluations spread over threads;
+ * the terms are added in bond order afterwards, so the result does not
+ * depend on the thread count. */
+double orc_local_energy_cnn_par(int L, double J1, double J2, int C, int D, const double *theta,
+                                int marshall, const int8_t *s, int *n_nbr, int nthreads)
+{
+    const int N = L * L;
+    double la; int sa;
+    orc_logpsi(L, C, D, theta, marshall, s, &la, &sa);
+    double *term = (double *)calloc((size_t)4 * N, sizeof(double));
+    double diag = 0.0;
+    int nn = 0;
+    for (int k = 0; k < 4 * N; ++k) {
+        const int i = k / 4, t = k % 4;
+        const int j = bond_partner(L, i / L, i % L, t);
+        const double J = (t < 2) ? J1 : J2;
+        if (s[i] == s[j]) diag += J / 4.0; else { diag -= J / 4.0; ++nn; }
+    }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int k = 0; k < 4 * N; ++k) {
+        const int i = k / 4, t = k % 4;
+        const int j = bond_partner(L, i / L, i % L, t);
+        if (s[i] == s[j]) continue;
+        const double J = (t < 2) ? J1 : J2;
+        int8_t *sp = (int8_t *)malloc((size_t)N);
+        memcpy(sp, s, (size_t)N);
+        sp[i] = s[j];
+        sp[j] = s[i];
+        double lb; int sb;
+        orc_logpsi(L, C, D, theta, marshall, sp, &lb, &sb);
+        term[k] = (J / 2.0) * ((double)sb / (double)sa) * exp(lb - la);
+        free(sp);
+    }
+    double e = diag;
+    for (int k = 0; k < 4 * N; ++k) e += term[k];
+    free(term);
+    if (n_nbr) *n_nbr = nn;
+    return e;
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

@@ -17,8 +17,8 @@ LIB_PATH = os.path.join(HERE, "libvmc.so")
 
 VMC_OK, VMC_ERR_ARG, VMC_ERR_CUDA, VMC_ERR_NONFINITE, VMC_ERR_TIMEOUT, VMC_ERR_STATE, VMC_ERR_UNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6
-VMC_FP64, VMC_FP32, VMC_BF16 = 0, 1, 2
-PRECISIONS = {"fp64": VMC_FP64, "fp32": VMC_FP32, "bf16": VMC_BF16}
+VMC_FP64, VMC_FP32, VMC_BF16, VMC_FP16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": VMC_FP64, "fp32": VMC_FP32, "bf16": VMC_BF16, "fp16": VMC_FP16}
 ERR_NAMES = {-1: "VMC_ERR_ARG", -2: "VMC_ERR_CUDA", -3: "VMC_ERR_NONFINITE", -4: "VMC_ERR_TIMEOUT",
              -5: "VMC_ERR_STATE", -6: "VMC_ERR_UNSUPPORTED"}
 

@@ -3,6 +3,7 @@
 // flipped/transposed for the backward), bias arrays and, for BF16
 // contexts, the tcgen05 B-operand images.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include "vmc_internal.h"
 #include "simt_common.cuh"
 #include "tc_layout.cuh"
@@ -50,7 +51,7 @@ __global__ void simt_image_kernel(const double *__restrict__ theta, T *fwd, T *b
     }
 }
 
-__global__ void tc_image_kernel(const double *__restrict__ theta, uint16_t *img, float *bias32, int C, int D)
+__global__ void tc_image_kernel(const double *__restrict__ theta, uint16_t *img, float *bias32, int C, int D, int f16)
 {
     const int64_t total = tc_wimg_bytes(C, D) / 2;
     const int64_t cb = tc_chunk_bytes(C);
@@ -76,7 +77,7 @@ __global__ void tc_image_kernel(const double *__restrict__ theta, uint16_t *img,
             const int ci = 16 * h + k;
             w = W[(n * C + ci) * 9 + tap];
         }
-        img[e] = __bfloat16_as_ushort(__double2bfloat16(w));
+        img[e] = f16 ? __half_as_ushort(__double2half(w)) : __bfloat16_as_ushort(__double2bfloat16(w));
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)(D + 1) * C; i += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(i / C), c = (int)(i % C);
@@ -103,8 +104,9 @@ int vmc_prepare_params(vmc_ctx *ctx, const void *theta, int dtype, cudaStream_t 
         vmc::simt_image_kernel<float><<<grid, blk, 0, s>>>(ctx->theta64, (float *)ctx->wsimt, (float *)ctx->wsimtT,
                                                            (float *)ctx->bias, C, D, CO);
     ctx->launches += 2;
-    if (ctx->arch.precision == VMC_BF16) {
-        vmc::tc_image_kernel<<<grid, blk, 0, s>>>(ctx->theta64, ctx->wimg, ctx->bias32, C, D);
+    if (vmc_is_tc(ctx->arch.precision)) {
+        vmc::tc_image_kernel<<<grid, blk, 0, s>>>(ctx->theta64, ctx->wimg, ctx->bias32, C, D,
+                                                  ctx->arch.precision == VMC_FP16);
         ctx->launches += 1;
     }
     return vmc_cuda_check(ctx, cudaGetLastError(), "prepare params");

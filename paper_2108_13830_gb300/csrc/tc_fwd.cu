@@ -25,6 +25,7 @@
 // is bounded by a time budget; on expiry the CTA raises VMC_ERR_TIMEOUT,
 // drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <algorithm>
 #include <vector>
 #include "vmc_internal.h"
@@ -97,10 +98,17 @@ struct Ctrl {
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t bf16x2(float a, float b)
+// two FP32 values -> packed 16-bit pair (low half = a), round to nearest even
+template <bool F16>
+__device__ __forceinline__ uint32_t pack2(float a, float b)
 {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&h);
+    if constexpr (F16) {
+        const __half2 h = __floats2half2_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        return *reinterpret_cast<const uint32_t *>(&h);
+    }
 }
 
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
@@ -110,7 +118,7 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 
 __device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
 
-template <int C>
+template <int C, bool F16>
 struct Kern {
     static constexpr uint32_t WB = 9 * (C / 16) * 32 * C;   // bytes of one C -> C layer image
     static constexpr int HALF = C / 2;                       // columns per epilogue thread
@@ -138,30 +146,32 @@ struct Kern {
     {
         const SlabMeta &m = c.slab[s];
         const int T = m.T, PW = m.PW;
-        const uint32_t idesc = idesc_bf16(128, C);
+        const uint32_t idesc = idesc_f16kind(128, C, F16);
         const uint32_t wb = smem_u32(smem + bsel * WB);
         const uint32_t dcol0 = tmem + (uint32_t)(s * p.Tcap * C);
         if (l == 0) {
             const uint32_t a0 = smem_u32(act_buf(s, 1));
-            const uint32_t lbo = 128u * T * 16u;
+            const uint64_t ad0 = smem_desc(a0, 128u * T * 16u, 128);
             const uint64_t bdesc = smem_desc(wb, 16 * C, 128);
             for (int t = 0; t < T; ++t)
-                umma_bf16(dcol0 + t * C, smem_desc(a0 + t * 2048u, lbo, 128), bdesc, idesc, 0);
+                umma_bf16(dcol0 + t * C, ad0 + (uint64_t)(t * 128), bdesc, idesc, 0);
         } else {
-            const uint32_t in = smem_u32(act_buf(s, (l - 1) & 1));
+            // descriptors differ from the base only in the start-address
+            // field (16-byte units), so each MMA needs two integer adds
+            const uint64_t ad0 = smem_desc(smem_u32(act_buf(s, (l - 1) & 1)), PS, 128);
+            const uint64_t bd0 = smem_desc(wb, 16 * C, 128);
+            const uint32_t plane2 = (2u * PS) >> 4;
             for (int t = 0; t < T; ++t) {
-                uint32_t k = 0;
-#pragma unroll 1
+                const uint32_t d = dcol0 + t * C;
+                const uint32_t rt = (uint32_t)(t * 128);
+#pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int ky = tap / 3, kx = tap - 3 * ky;
-                    const uint32_t row0 = (uint32_t)(t * 128 + ky * PW + kx);
+                    const uint32_t roff = rt + (uint32_t)(ky * PW + kx);
 #pragma unroll
-                    for (int h = 0; h < C / 16; ++h) {
-                        const uint64_t adesc = smem_desc(in + 2u * h * PS + row0 * 16u, PS, 128);
-                        const uint64_t bdesc = smem_desc(wb + (uint32_t)(tap * (C / 16) + h) * 32u * C, 16 * C, 128);
-                        umma_bf16(dcol0 + t * C, adesc, bdesc, idesc, k);
-                        ++k;
-                    }
+                    for (int h = 0; h < C / 16; ++h)
+                        umma_bf16(d, ad0 + (uint64_t)(roff + h * plane2),
+                                  bd0 + (uint64_t)((tap * (C / 16) + h) * 2 * C), idesc, (tap | h) != 0);
                 }
             }
         }
@@ -265,7 +275,7 @@ struct Kern {
                     const float h0 = 0.5f * (v[2 * i] + bb[2 * i]), h1 = 0.5f * (v[2 * i + 1] + bb[2 * i + 1]);
                     const float a0 = fmaf(h0, tanh_approx(h0), h0);   // SiLU(z) = (z/2)(1 + tanh(z/2))
                     const float a1 = fmaf(h1, tanh_approx(h1), h1);
-                    w[i] = bf16x2(a0, a1);
+                    w[i] = pack2<F16>(a0, a1);
                 }
                 const int R0 = (y + 1) * PW + j * (L + 2) + x + 1;
                 int rows[4];
@@ -421,7 +431,7 @@ struct Kern {
                     int v = spins[site];
                     if (site == bi) v = spins[bj];
                     else if (site == bj) v = spins[bi];
-                    h[ky * 3 + kx] = v > 0 ? 0x3F80u : 0xBF80u;
+                    h[ky * 3 + kx] = F16 ? (v > 0 ? 0x3C00u : 0xBC00u) : (v > 0 ? 0x3F80u : 0xBF80u);
                 }
             }
             const uint32_t q = (uint32_t)(y * PW + jj * (L + 2) + x) * 16u;
@@ -586,13 +596,13 @@ struct Kern {
     }
 };
 
-template <int C>
+template <int C, bool F16>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_constant__ Params p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t BUF = (uint32_t)(C / 8) * p.Rcap * 16u;
-    Ctrl &c = *reinterpret_cast<Ctrl *>(smem + 2 * Kern<C>::WB + (size_t)2 * p.S * BUF);
+    Ctrl &c = *reinterpret_cast<Ctrl *>(smem + 2 * Kern<C, F16>::WB + (size_t)2 * p.S * BUF);
     int8_t *spins = reinterpret_cast<int8_t *>(&c + 1);
     uint16_t *list = reinterpret_cast<uint16_t *>(spins + ((p.L_max * p.L_max + 15) & ~15));
     if (tid == 0) {
@@ -615,7 +625,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    Kern<C> k(p, smem, c, spins, list, BUF, c.tmem_base);
+    Kern<C, F16> k(p, smem, c, spins, list, BUF, c.tmem_base);
     if (warp < 8) k.epilogue_role(tid);
     else if ((tid & 31) == 0) k.mma_role();
     tc_fence_before();
@@ -715,7 +725,7 @@ static int make_plan(const vmc_ctx *ctx, int L_main, int L_max, bool ragged, Pla
     return VMC_OK;
 }
 
-template <int C>
+template <int C, bool F16>
 static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, const int64_t *offs,
                   const int32_t *Ls, int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr,
                   cudaStream_t st, int grid_override)
@@ -732,7 +742,7 @@ static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, c
     p.out_a = out_a; p.out_sign = static_cast<int8_t *>(out_b); p.n_nbr = n_nbr;
     p.status = ctx->status; p.counter = ctx->counter;
     p.budget_ns = ctx->wait_budget_ns;
-    auto kfn = tc_eloc_kernel<C>;
+    auto kfn = tc_eloc_kernel<C, F16>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
     if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "cudaFuncSetAttribute(tc_eloc)");
     e = cudaMemsetAsync(ctx->counter, 0, sizeof(int), st);
@@ -742,6 +752,18 @@ static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, c
     kfn<<<grid, NTHREADS, pl.smem, st>>>(p);
     ctx->launches += 1;
     return vmc_cuda_check(ctx, cudaGetLastError(), "tc_eloc launch");
+}
+
+static int launch_any(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, const int64_t *offs,
+                      const int32_t *Ls, int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr,
+                      cudaStream_t st)
+{
+    const bool f16 = ctx->arch.precision == VMC_FP16;
+    if (ctx->arch.channels == 32)
+        return f16 ? launch<32, true>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st, 0)
+                   : launch<32, false>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st, 0);
+    return f16 ? launch<16, true>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st, 0)
+               : launch<16, false>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st, 0);
 }
 
 // ------------------------------------------------------------------ diagnostics
@@ -856,9 +878,7 @@ int vmc_tc_eloc(vmc_ctx *ctx, int mode, const int8_t *sigma, const int64_t *offs
     const bool ragged = (Ls != nullptr);
     int rc = tc::make_plan(ctx, ragged ? L_max : ctx->L, L_max, ragged, &pl);
     if (rc) return vmc_fail(ctx, rc, "no tensor-core plan for L=%d C=%d", L_max, ctx->arch.channels);
-    if (ctx->arch.channels == 32)
-        return tc::launch<32>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, s, 0);
-    return tc::launch<16>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, s, 0);
+    return tc::launch_any(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, s);
 }
 
 int vmc_tc_debug_timeout(vmc_ctx *ctx, int64_t budget_ns, cudaStream_t s)
@@ -888,11 +908,10 @@ extern "C" int vmc_debug_umma_selftest(const uint16_t *A_dev, const uint16_t *B_
 extern "C" int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream)
 {
     if (!ctx || L < 4 || L > 32 || (L & 1) || probe_B < 1) return VMC_ERR_ARG;
-    if (ctx->arch.precision != VMC_BF16) return vmc_fail(ctx, VMC_ERR_STATE, "autotune applies to BF16 contexts");
+    if (!vmc_is_tc(ctx->arch.precision)) return vmc_fail(ctx, VMC_ERR_STATE, "autotune applies to tensor-core contexts");
     if (!ctx->params_set) return vmc_fail(ctx, VMC_ERR_STATE, "parameters not set");
     ctx->launches = 0;
     cudaStream_t st = (cudaStream_t)stream;
-    const int C = ctx->arch.channels;
     const size_t cfg_bytes = (size_t)probe_B * L * L, out_bytes = (size_t)probe_B * 8;
     char *buf = nullptr;
     if (cudaMalloc(&buf, cfg_bytes + out_bytes + 256) != cudaSuccess) return vmc_fail(ctx, VMC_ERR_CUDA, "autotune alloc");
@@ -920,8 +939,7 @@ extern "C" int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream)
             float ms = 0.f;
             for (int rep = 0; rep < 3 && rc == VMC_OK; ++rep) {
                 cudaEventRecord(e0, st);
-                rc = (C == 32) ? tc::launch<32>(ctx, pl, 1, cfg, nullptr, nullptr, probe_B, L, out, nullptr, nullptr, st, 0)
-                               : tc::launch<16>(ctx, pl, 1, cfg, nullptr, nullptr, probe_B, L, out, nullptr, nullptr, st, 0);
+                rc = tc::launch_any(ctx, pl, 1, cfg, nullptr, nullptr, probe_B, L, out, nullptr, nullptr, st);
                 cudaEventRecord(e1, st);
                 cudaEventSynchronize(e1);
                 cudaEventElapsedTime(&ms, e0, e1);

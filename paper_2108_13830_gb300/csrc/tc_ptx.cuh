@@ -156,12 +156,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, dense, shape M x N.
-__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
+// Instruction descriptor of kind::f16: FP32 accumulator, A and B both BF16
+// (format 1) or both FP16 (format 0), K-major, dense, shape M x N.
+__host__ __device__ __forceinline__ uint32_t idesc_f16kind(int M, int N, bool fp16)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    const uint32_t fmt = fp16 ? 0u : 1u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int M, int N) { return idesc_f16kind(M, N, false); }
 
 __device__ __forceinline__ float tanh_approx(float x)
 {

@@ -50,8 +50,8 @@ static bool arch_ok(int L, const vmc_arch *a, char *why, size_t nw)
     if (L < 4 || L > 32 || (L & 1)) { snprintf(why, nw, "L=%d must be even, 4..32", L); return false; }
     if (a->n_layers_cc < 1 || a->n_layers_cc > 64) { snprintf(why, nw, "n_layers_cc=%d out of 1..64", a->n_layers_cc); return false; }
     if (a->channels < 4 || a->channels > 64 || a->channels % 4) { snprintf(why, nw, "channels=%d must be a multiple of 4 in 4..64", a->channels); return false; }
-    if (a->precision != VMC_FP64 && a->precision != VMC_FP32 && a->precision != VMC_BF16) { snprintf(why, nw, "bad precision %d", a->precision); return false; }
-    if (a->precision == VMC_BF16 && (a->channels != 16 && a->channels != 32)) { snprintf(why, nw, "BF16 path supports channels 16 or 32"); return false; }
+    if (a->precision < VMC_FP64 || a->precision > VMC_FP16) { snprintf(why, nw, "bad precision %d", a->precision); return false; }
+    if (vmc_is_tc(a->precision) && (a->channels != 16 && a->channels != 32)) { snprintf(why, nw, "tensor-core path supports channels 16 or 32"); return false; }
     if (a->marshall_sign != 0 && a->marshall_sign != 1) { snprintf(why, nw, "marshall_sign must be 0 or 1"); return false; }
     return true;
 }
@@ -89,7 +89,7 @@ int vmc_create(int L, double J1, double J2, const vmc_arch *arch, vmc_ctx **out)
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(DevStatus));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->counter, 64 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 64 * sizeof(int));
-    if (e == cudaSuccess && arch->precision == VMC_BF16) {
+    if (e == cudaSuccess && vmc_is_tc(arch->precision)) {
         ctx->wimg_bytes = (size_t)(32LL * C + (int64_t)D * 9 * (C / 16) * 32LL * C);
         e = cudaMalloc(&ctx->wimg, ctx->wimg_bytes);
     }
@@ -152,7 +152,7 @@ int vmc_logpsi(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B, double *logabs_
     if (B < 0) return vmc_fail(ctx, VMC_ERR_ARG, "negative batch");
     if (B == 0) return VMC_OK;
     if (!sigma_dev || !logabs_dev || !sign_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
-    if (ctx->arch.precision == VMC_BF16)
+    if (vmc_is_tc(ctx->arch.precision))
         return vmc_tc_eloc(ctx, 0, sigma_dev, nullptr, nullptr, B, ctx->L, logabs_dev, sign_dev, nullptr, (cudaStream_t)stream);
     return vmc_simt_eloc(ctx, 0, sigma_dev, nullptr, nullptr, B, ctx->L, logabs_dev, sign_dev, nullptr, (cudaStream_t)stream);
 }
@@ -164,7 +164,7 @@ int vmc_local_energy(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B, double *e
     if (B < 0) return vmc_fail(ctx, VMC_ERR_ARG, "negative batch");
     if (B == 0) return VMC_OK;
     if (!sigma_dev || !eloc_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
-    if (ctx->arch.precision == VMC_BF16)
+    if (vmc_is_tc(ctx->arch.precision))
         return vmc_tc_eloc(ctx, 1, sigma_dev, nullptr, nullptr, B, ctx->L, eloc_dev, nullptr, n_nbr_dev, (cudaStream_t)stream);
     return vmc_simt_eloc(ctx, 1, sigma_dev, nullptr, nullptr, B, ctx->L, eloc_dev, nullptr, n_nbr_dev, (cudaStream_t)stream);
 }
@@ -178,7 +178,7 @@ int vmc_local_energy_ragged(vmc_ctx *ctx, const int8_t *packed_dev, const int64_
     if (B == 0) return VMC_OK;
     if (!packed_dev || !offs_dev || !L_dev || !eloc_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
     if (L_max < 4 || L_max > 32 || (L_max & 1)) return vmc_fail(ctx, VMC_ERR_ARG, "L_max=%d must be even, 4..32", L_max);
-    if (ctx->arch.precision == VMC_BF16)
+    if (vmc_is_tc(ctx->arch.precision))
         return vmc_tc_eloc(ctx, 1, packed_dev, offs_dev, L_dev, B, L_max, eloc_dev, nullptr, n_nbr_dev, (cudaStream_t)stream);
     return vmc_simt_eloc(ctx, 1, packed_dev, offs_dev, L_dev, B, L_max, eloc_dev, nullptr, n_nbr_dev, (cudaStream_t)stream);
 }

@@ -52,7 +52,7 @@ struct vmc_ctx {
     void *wsimt = nullptr;       // SIMT forward weights, [l][cblk][ci][9][CO] (float or double)
     void *wsimtT = nullptr;      // transposed/flipped weights for the backward grad-input conv
     void *bias = nullptr;        // [(D+1)][C] (float or double, matching the SIMT type)
-    uint16_t *wimg = nullptr;    // BF16 UMMA B-operand images, all layers
+    uint16_t *wimg = nullptr;    // BF16 / FP16 UMMA B-operand images, all layers
     float *bias32 = nullptr;     // [(D+1)][C] FP32 biases for the tensor-core epilogue
     size_t wimg_bytes = 0;
 
@@ -113,5 +113,6 @@ int vmc_ot_vec_impl(vmc_ctx *ctx, const float *O, int64_t m, const double *w, do
 int vmc_sr_solve_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m, double shift,
                       int iters, double *x, double *resid_out, cudaStream_t s);
 
+__host__ __device__ static inline bool vmc_is_tc(int precision) { return precision == VMC_BF16 || precision == VMC_FP16; }
 __host__ __device__ static inline int64_t vmc_nparams(int C, int D) { return (int64_t)10 * C + (int64_t)D * (9 * C * C + C); }
 __host__ __device__ static inline int64_t vmc_woffset(int C, int l) { return l == 0 ? 0 : (int64_t)10 * C + (int64_t)(l - 1) * (9 * C * C + C); }

@@ -44,7 +44,7 @@ WORKLOADS = {
     "L4_fp64": Workload("L4_fp64", 4, 4, 2, "fp64", 256, index=0),
     "L10_fp32": Workload("L10_fp32", 10, 16, 6, "fp32", 4096, index=1),
     "L16_bf16": Workload("L16_bf16", 16, 32, 8, "bf16", 8192, index=2),
-    "ragged_8_16": Workload("ragged_8_16", 16, 16, 6, "bf16", 2048, kind="ragged",
+    "ragged_8_16": Workload("ragged_8_16", 16, 16, 6, "fp16", 2048, kind="ragged",
                             Ls=(8, 10, 12, 16), index=3),
     "L24_bf16_sr": Workload("L24_bf16_sr", 24, 32, 10, "bf16", 4096, index=4),
 }

@@ -1,0 +1,132 @@
+"""Full-size workloads in the launch configuration bench.py times.
+
+L = 16 (C = 32, D = 8, 8192 samples) and L = 24 (C = 32, D = 10, 4096
+samples) in BF16, the mixed-size batch (2048 samples of each of L = 8, 10,
+12, 16; 16 channels, 6 layers) in FP16: every sample's neighbour count
+exactly, E_loc/site of sampled parents within 5e-4 of the FP64 oracle, the
+batch-mean energy of BF16 within 1e-5 per site of the FP32 path (whose
+per-sample error is <= 1e-6), O_k rows against the oracle, and the SR solve
+on the full O through its true residual.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2108_13830_gb300 import inputs
+from paper_2108_13830_gb300.binding import VMC_OK
+from gpu_util import bond_counts, make_ctx, to_dev
+
+pytestmark = pytest.mark.gpu
+
+NTH = os.cpu_count() or 8
+
+
+@pytest.fixture(scope="module")
+def l16():
+    w = inputs.WORKLOADS["L16_bf16"]
+    sig, theta = inputs.workload_inputs(w)
+    v = make_ctx(w, theta=theta)
+    s = to_dev(sig)
+    e, nn = v.local_energy(s)
+    assert v.sync_status()[0] == VMC_OK
+    return w, sig, theta, v, s, e.cpu().numpy(), nn.cpu().numpy()
+
+
+def test_l16_neighbour_counts(l16):
+    w, sig, theta, v, s, e, nn = l16
+    a1, a2 = bond_counts(sig)
+    np.testing.assert_array_equal(nn, a1 + a2)
+    assert np.all(np.isfinite(e))
+
+
+def test_l16_bf16_sampled_parents_vs_oracle(l16):
+    w, sig, theta, v, s, e, nn = l16
+    pick = np.random.default_rng(16).choice(w.batch, 6, replace=False)
+    re, rn = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
+    np.testing.assert_array_equal(nn[pick], rn)
+    err = np.abs(e[pick] - re) / (w.L * w.L)
+    assert err.max() <= 5e-4, err
+
+
+def test_l16_bf16_mean_energy_vs_fp32(l16):
+    w, sig, theta, v, s, e, nn = l16
+    B = 2048
+    v32 = make_ctx(w, precision="fp32", theta=theta)
+    e32, _ = v32.local_energy(s[:B])
+    assert v32.sync_status()[0] == VMC_OK
+    e32 = e32.cpu().numpy()
+    N = w.L * w.L
+    assert abs((e[:B] - e32).mean()) / N <= 1e-5
+    pick = np.random.default_rng(17).choice(B, 2, replace=False)
+    re, _ = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
+    assert (np.abs(e32[pick] - re) / N).max() <= 1e-6
+
+
+def test_l16_log_derivs_rows(l16):
+    w, sig, theta, v, s, e, nn = l16
+    O = v.log_derivs(s)                      # full batch, [8192, 74304] FP32
+    assert torch.isfinite(O).all().item()
+    rows = [0, w.batch - 1]
+    R = oracle.log_derivs(w.L, w.C, w.D, theta, sig[rows], nthreads=NTH)
+    Og = O[rows].double().cpu().numpy()
+    rel = np.abs(Og - R).max(axis=1) / np.abs(R).max(axis=1)
+    assert rel.max() <= 1e-6, rel
+
+
+@pytest.fixture(scope="module")
+def l24():
+    w = inputs.WORKLOADS["L24_bf16_sr"]
+    sig, theta = inputs.workload_inputs(w)
+    v = make_ctx(w, theta=theta)
+    s = to_dev(sig)
+    e, nn = v.local_energy(s)
+    assert v.sync_status()[0] == VMC_OK
+    return w, sig, theta, v, s, e, nn.cpu().numpy()
+
+
+def test_l24_bf16_sampled_parents_vs_oracle(l24):
+    w, sig, theta, v, s, e, nn = l24
+    a1, a2 = bond_counts(sig)
+    np.testing.assert_array_equal(nn, a1 + a2)
+    pick = np.random.default_rng(24).choice(w.batch, 2, replace=False)
+    re, rn = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
+    err = np.abs(e.cpu().numpy()[pick] - re) / (w.L * w.L)
+    assert err.max() <= 5e-4, err
+
+
+def test_l24_log_derivs_and_sr(l24):
+    w, sig, theta, v, s, e, nn = l24
+    O = v.log_derivs(s)                      # [4096, 92800] FP32, 1.52 GB
+    R = oracle.log_derivs(w.L, w.C, w.D, theta, sig[:1], nthreads=NTH)
+    rel = np.abs(O[0].double().cpu().numpy() - R[0]).max() / np.abs(R[0]).max()
+    assert rel <= 1e-6
+    x, res = v.sr_solve(O, e, w.shift, w.cg_iters)
+    assert v.sync_status()[0] == VMC_OK
+    # true residual of x with the oracle's FP64 covariance product on the full O
+    Od = O.double().cpu().numpy()
+    ob, _, g = oracle.sr_moments(Od, e.cpu().numpy())
+    r = g - oracle.sr_matvec(Od, ob, x.cpu().numpy(), w.shift)
+    true_res = np.linalg.norm(r) / np.linalg.norm(g)
+    assert true_res < 1.0
+    assert abs(res - true_res) <= 0.05 * true_res + 1e-12
+
+
+def test_ragged_full_batch():
+    w = inputs.WORKLOADS["ragged_8_16"]
+    packed, offs, Ls, theta = inputs.ragged_inputs(w)
+    v = make_ctx(w, theta=theta, L=16)
+    e, nn = v.local_energy_ragged(to_dev(packed), to_dev(offs), to_dev(Ls), 16)
+    assert v.sync_status()[0] == VMC_OK
+    e, nn = e.cpu().numpy(), nn.cpu().numpy()
+    assert np.all(np.isfinite(e))
+    for L in w.Ls:
+        idx = np.where(Ls == L)[0]
+        cfg = np.stack([packed[offs[b]:offs[b] + L * L].reshape(L, L) for b in idx])
+        a1, a2 = bond_counts(cfg)
+        np.testing.assert_array_equal(nn[idx], a1 + a2)
+        b = idx[len(idx) // 2]
+        re, _ = oracle.local_energy_par(L, w.J1, w.J2, w.C, w.D, theta, cfg[len(idx) // 2][None], nthreads=NTH)
+        assert abs(e[b] - re[0]) / (L * L) <= 5e-4
