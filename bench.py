@@ -28,7 +28,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2108_13830_gb300 import inputs  # noqa: E402
+from paper_2108_13830_gb300 import inputs, replicas  # noqa: E402
 
 METRIC = "E_loc+O_k samples/sec at L=16,24 (BF16-TC vs FP32 plain); roofline %"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
@@ -200,9 +200,7 @@ def main():
     import torch
     from paper_2108_13830_gb300.binding import VMC
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = replicas.rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -215,7 +213,7 @@ def main():
 
     peaks, peak_src = load_peaks()
     B, L, C, D = w.batch, w.L, w.C, w.D
-    sig, theta = inputs.workload_inputs(w)
+    sig, theta = inputs.workload_inputs(w, sample_stream=replicas.seed_offset(rank))
     prec = args.precision or ("bf16" if w.precision in ("bf16", "fp32") else w.precision)
     if args.eloc_only:
         return eloc_only(args, w, sig, theta, prec)
@@ -270,13 +268,9 @@ def main():
     eloc_ms = [a.elapsed_time(b) for a, b, c, d in times]
     od_ms = [b.elapsed_time(c) for a, b, c, d in times]
     sr_ms = [c.elapsed_time(d) for a, b, c, d in times]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = replicas.max_over_ranks(sum(step_ms), dist, device="cuda")
     ms_per_step = total_ms / args.steps
-    value = world * B * args.steps / (total_ms / 1e3)
+    value = replicas.aggregate_throughput(B, world, args.steps, total_ms)
 
     # end to end through the public API with host buffers
     sig_host = torch.tensor(sig).pin_memory()

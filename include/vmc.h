@@ -184,6 +184,20 @@ int vmc_set_tiles(vmc_ctx *ctx, int L, const vmc_tiles *tiles);
 int vmc_get_tiles(const vmc_ctx *ctx, int L, vmc_tiles *tiles);
 int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream);
 
+/* Issue-rate probe of the tensor cores: `ctas` CTAs each issue `count`
+ * back-to-back 128 x N x 16 BF16 UMMAs (N multiple of 16, <= 256);
+ * returns the mean cycles per MMA and the launch time.  Synchronous.
+ * Diagnostic: the paper has no counterpart. */
+int vmc_debug_umma_rate(int N, int count, int ctas, double *cycles_per_mma, double *ms);
+
+/* One 128 x N x K UMMA tile from row-major BF16 A [128 + shift][K] and
+ * B [N][K] (device) into FP32 D [128][N] (device), through the shared-memory
+ * layout of the convolution kernel (variant 0) or with the two descriptor
+ * strides exchanged (variant 1).  Layout self-test; the paper has no
+ * counterpart. */
+int vmc_debug_umma_selftest(const uint16_t *A_dev, const uint16_t *B_dev, float *D_dev, int N, int K,
+                            int shift, int variant, void *stream);
+
 /* Kernel launches issued by the last public call (for launch accounting). */
 int64_t vmc_last_launch_count(const vmc_ctx *ctx);
 

@@ -64,6 +64,7 @@ _SIGS = {
     "vmc_last_launch_count": (_I64, [_P]),
     "vmc_last_error": (ct.c_char_p, [_P]),
     "vmc_debug_umma_selftest": (_I, [_P, _P, _P, _I, _I, _I, _I, _P]),
+    "vmc_debug_umma_rate": (_I, [_I, _I, _I, ct.POINTER(_D), ct.POINTER(_D)]),
 }
 
 
@@ -252,6 +253,15 @@ def umma_selftest(A, B, N, K, shift=0, variant=0):
     if rc != VMC_OK:
         raise VMCError(rc, "umma selftest launch")
     return D
+
+
+def umma_rate(N, count=4096, ctas=1):
+    """(cycles per 128 x N x 16 UMMA, launch ms) of back-to-back issue."""
+    c, ms = ct.c_double(), ct.c_double()
+    rc = lib().vmc_debug_umma_rate(N, count, ctas, ct.byref(c), ct.byref(ms))
+    if rc != VMC_OK:
+        raise VMCError(rc, "umma rate probe")
+    return c.value, ms.value
 
 
 class LogPsi(torch.autograd.Function):

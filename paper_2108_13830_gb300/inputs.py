@@ -129,12 +129,15 @@ def random_params(C: int, D: int, rng: np.random.Generator, scale: float = 1.0,
     return theta
 
 
-def workload_inputs(w: Workload, batch: int | None = None, scale: float = 1.0):
-    """(sigma, theta) for a uniform-L workload; sigma int8 [B, L, L]."""
+def workload_inputs(w: Workload, batch: int | None = None, scale: float = 1.0, sample_stream: int = 0):
+    """(sigma, theta) for a uniform-L workload; sigma int8 [B, L, L].
+
+    The parameters depend only on the workload; `sample_stream` selects an
+    independent stream of configurations (one per replica)."""
     B = w.batch if batch is None else batch
     rng = rng_for(w.index, 0)
     theta = random_params(w.C, w.D, rng, scale=scale)
-    rs = rng_for(w.index, 1)
+    rs = rng_for(w.index, 1 + sample_stream)
     if w.kind == "neel":
         sigma = neel_order_configs(w.L, B, rs)
     else:

@@ -3,7 +3,8 @@
 L = 16 (C = 32, D = 8, 8192 samples) and L = 24 (C = 32, D = 10, 4096
 samples) in BF16, the mixed-size batch (2048 samples of each of L = 8, 10,
 12, 16; 16 channels, 6 layers) in FP16: every sample's neighbour count
-exactly, E_loc/site of sampled parents within 5e-4 of the FP64 oracle, the
+exactly, E_loc/site of sampled parents within the per-sample tolerance of
+the FP64 oracle, the
 batch-mean energy of BF16 within 1e-5 per site of the FP32 path (whose
 per-sample error is <= 1e-6), O_k rows against the oracle, and the SR solve
 on the full O through its true residual.
@@ -42,12 +43,38 @@ def test_l16_neighbour_counts(l16):
     assert np.all(np.isfinite(e))
 
 
-def test_l16_bf16_sampled_parents_vs_oracle(l16):
+# Per-sample E_loc/site tolerances.  FP16 operands: 5e-4.  BF16 operands:
+# 5e-4 at L = 24; at L = 16 a CPU emulation of exact BF16 rounding (FP32
+# accumulation, exact SiLU) already reaches 5.8e-4 on one of six sampled
+# parents, so the per-sample bound there is 1e-3 while the batch-mean bound
+# (1e-5 per site) is unchanged.
+L16_BF16_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def l16_pick(l16):
     w, sig, theta, v, s, e, nn = l16
     pick = np.random.default_rng(16).choice(w.batch, 6, replace=False)
     re, rn = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
+    return pick, re, rn
+
+
+def test_l16_bf16_sampled_parents_vs_oracle(l16, l16_pick):
+    w, sig, theta, v, s, e, nn = l16
+    pick, re, rn = l16_pick
     np.testing.assert_array_equal(nn[pick], rn)
     err = np.abs(e[pick] - re) / (w.L * w.L)
+    assert err.max() <= L16_BF16_TOL, err
+    assert np.median(err) <= 5e-4, err
+
+
+def test_l16_fp16_sampled_parents_vs_oracle(l16, l16_pick):
+    w, sig, theta, v, s, e, nn = l16
+    pick, re, rn = l16_pick
+    v16 = make_ctx(w, precision="fp16", theta=theta)
+    e16, _ = v16.local_energy(s[torch.as_tensor(pick, device="cuda")])
+    assert v16.sync_status()[0] == VMC_OK
+    err = np.abs(e16.cpu().numpy() - re) / (w.L * w.L)
     assert err.max() <= 5e-4, err
 
 
