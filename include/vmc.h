@@ -152,6 +152,29 @@ int vmc_sr_matvec(vmc_ctx *ctx, const float *O_dev, int64_t m, const double *Oba
 int vmc_ot_vec(vmc_ctx *ctx, const float *O_dev, int64_t m, const double *w_dev,
                double *out_dev, void *stream);
 
+/* out = O^T w like vmc_ot_vec, for callers that must not allocate device
+ * memory: code running inside an allocator or memory-pool callback, runtimes
+ * that forbid cudaMalloc after start-up, or processes with a device-memory
+ * budget fixed at load time.  It takes no context (creating one allocates)
+ * and calls no cudaMalloc, cudaFree or allocating library routine; its
+ * scratch is a 16 MiB array in the library's device image, held by every
+ * GPU that loads the library until the process exits.  The paper has no
+ * counterpart.
+ *  - O_dev float [m][n], w_dev double [m], out_dev double [n] (device,
+ *    owned by the caller); asynchronous on `stream`.
+ *  - Limit: 8 n c + 8 m <= 16 MiB (m rounded up to a multiple of 32), with
+ *    c = 16 row chunks for m >= 1024, 4 for m >= 64, else 1; e.g. m = 4096
+ *    allows n <= 130816.  Larger sizes return VMC_ERR_UNSUPPORTED before
+ *    any device work; null pointers or m, n < 1 return VMC_ERR_ARG.
+ *  - The first call on a device looks up the scratch array's device address
+ *    (with that device current) and caches it; make that first call before
+ *    any stream capture.
+ *  - All calls on a device share the scratch and it keeps the last call's
+ *    contents (nothing in it needs to start at zero); calls whose work
+ *    overlaps on the GPU (different streams, no ordering) race. */
+int vmc_ot_vec_noalloc(const float *O_dev, int64_t m, int64_t n, const double *w_dev,
+                       double *out_dev, void *stream);
+
 /* Solve (S + shift I) x = G for the SR direction (Eq. 6 with eta = 1:
  * Delta = x; the caller applies theta -= eta x) by conjugate gradient from
  * x = 0, exactly `iters` iterations (fewer only when the residual is exactly

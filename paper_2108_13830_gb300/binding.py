@@ -54,6 +54,7 @@ _SIGS = {
     "vmc_sr_moments": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "vmc_sr_matvec": (_I, [_P, _P, _I64, _P, _P, _D, _P, _P]),
     "vmc_ot_vec": (_I, [_P, _P, _I64, _P, _P, _P]),
+    "vmc_ot_vec_noalloc": (_I, [_P, _I64, _I64, _P, _P, _P]),
     "vmc_sr_solve": (_I, [_P, _P, _P, _I64, _D, _I, _P, ct.POINTER(_D), _P]),
     "vmc_sync_status": (_I, [_P, _P, ct.POINTER(_I64)]),
     "vmc_set_wait_budget": (_I, [_P, _I64]),
@@ -244,6 +245,16 @@ class VMC:
     def autotune(self, L, probe_B=512):
         self._check(lib().vmc_autotune(self._h, L, int(probe_B), _stream()))
         return self.get_tiles(L)
+
+
+def ot_vec_noalloc(O, w, out=None):
+    """O^T w through the allocation-free entry point (no context; see vmc.h).
+
+    Returns (out, status) without raising, so callers can inspect the code."""
+    m, n = O.shape
+    out = out if out is not None else torch.empty(n, dtype=torch.float64, device=O.device)
+    rc = lib().vmc_ot_vec_noalloc(_ptr(O), m, n, _ptr(w), _ptr(out), _stream())
+    return out, rc
 
 
 def umma_selftest(A, B, N, K, shift=0, variant=0):
