@@ -213,8 +213,8 @@ int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream);
  * Diagnostic: the paper has no counterpart. */
 int vmc_debug_umma_rate(int N, int count, int ctas, double *cycles_per_mma, double *ms);
 
-/* One 128 x N x K UMMA tile from row-major BF16 A [128 + shift][K] and
- * B [N][K] (device) into FP32 D [128][N] (device), through the shared-memory
+/* One 128 x N x K UMMA tile (N multiple of 16 up to 128, K = 16 or 32)
+ * from row-major BF16 A [128 + shift][K] and B [N][K] (device) into FP32 D [128][N] (device), through the shared-memory
  * layout of the convolution kernel (variant 0) or with the two descriptor
  * strides exchanged (variant 1).  Layout self-test; the paper has no
  * counterpart. */

@@ -54,18 +54,20 @@ __global__ void simt_image_kernel(const double *__restrict__ theta, T *fwd, T *b
 __global__ void tc_image_kernel(const double *__restrict__ theta, uint16_t *img, float *bias32, int C, int D, int f16)
 {
     const int64_t total = tc_wimg_bytes(C, D) / 2;
-    const int64_t cb = tc_chunk_bytes(C);
+    const int64_t l0 = tc_layer_bytes(C, 0), l1 = tc_layer_bytes(C, 1);
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t byte = 2 * e;
         int l;
         int64_t rb;
-        if (byte < cb) { l = 0; rb = byte; }
-        else { l = 1 + (int)((byte - cb) / tc_layer_bytes(C, 1)); rb = (byte - cb) - (int64_t)(l - 1) * tc_layer_bytes(C, 1); }
+        if (byte < l0) { l = 0; rb = byte; }
+        else { l = 1 + (int)((byte - l0) / l1); rb = (byte - l0) - (int64_t)(l - 1) * l1; }
+        const int N = tc_chunk_n(C, l);
+        const int64_t cb = tc_chunk_bytes(C, l);
         const int chunk = (int)(rb / cb);
         const int off = (int)(rb % cb);
-        // invert tc_b_elem_offset: off = kg*16C + ng*128 + nr*16 + kr*2
-        const int kg = off / (16 * C);
-        const int rem = off % (16 * C);
+        // invert tc_b_elem_offset: off = kg*16N + ng*128 + nr*16 + kr*2
+        const int kg = off / (16 * N);
+        const int rem = off % (16 * N);
         const int n = (rem / 128) * 8 + (rem % 128) / 16;
         const int k = kg * 8 + (rem % 16) / 2;
         double w = 0.0;
@@ -73,9 +75,10 @@ __global__ void tc_image_kernel(const double *__restrict__ theta, uint16_t *img,
         if (l == 0) {
             if (k < 9) w = W[n * 9 + k];
         } else {
-            const int tap = chunk / (C / 16), h = chunk % (C / 16);
+            const int ky = chunk / (C / 16), h = chunk % (C / 16);
+            const int kx = n / C, co = n % C;
             const int ci = 16 * h + k;
-            w = W[(n * C + ci) * 9 + tap];
+            w = W[(co * C + ci) * 9 + ky * 3 + kx];
         }
         img[e] = f16 ? __half_as_ushort(__double2half(w)) : __bfloat16_as_ushort(__double2bfloat16(w));
     }

@@ -1,5 +1,5 @@
-// Tensor-core (tcgen05, BF16 x BF16 -> FP32) forward pass, log|psi| and
-// local energy: the hot loop of Sec. 3.1 ("sprime_batch") on sm_103a.
+// Tensor-core (tcgen05, BF16/FP16 x BF16/FP16 -> FP32) forward pass, log|psi|
+// and local energy: the hot loop of Sec. 3.1 ("sprime_batch") on sm_103a.
 //
 // Persistent CTAs, one per SM.  Each CTA pulls sampled configurations
 // sigma from a global counter; for each it lists the antiparallel J1/J2
@@ -8,22 +8,28 @@
 // into "slabs": G lattices side by side, each as (L+2) x (L+2) circularly
 // padded cells, so a slab is a PH x PW grid with PW = G (L+2), PH = L+2.
 //
-// A C -> C layer is an implicit GEMM per 128-row tile of the slab:
-// D[q][co] = sum_{tap, ci} A[q + ky PW + kx][ci] * W[tap][ci][co], where
-// q indexes padded cells row-major (outputs at junk columns are computed
-// and dropped).  The tap shift is a start-address offset of the A
-// descriptor (tc_layout.cuh), so no im2col copy exists; K = 9 C in chunks
-// of 16, N = C, FP32 accumulators in TMEM.  The embedding layer (c_in = 1)
-// uses a small im2col of the nine spins (K = 16, 7 zero).
+// A C -> C layer is an implicit GEMM over tiles of 128 padded cells
+// (row-major, tile t starting at cell 126 t):
+//   P[q][kx C + co] = sum_{ky, ci} A[q + ky PW][ci] W[ky][kx][ci][co]
+// (the vertical tap is a start-address offset of the A descriptor, the
+// three horizontal taps are stacked along N = 3 C), so a tile takes 3 C/16
+// MMAs of 128 x 3C x 16.  The output of cell q is
+//   z[q][co] = P[q][co] + P[q+1][C + co] + P[q+2][2C + co],
+// which the epilogue forms across TMEM lanes with warp shuffles (the last
+// two rows of a tile are overlap rows, hence the stride 126).  Outputs at
+// the padding columns are computed and dropped.  The embedding layer
+// (c_in = 1) uses a small im2col of the nine spins (K = 16, 7 zero).
 //
-// Warp roles: warps 0-7 (the "epilogue" group) build neighbours, drain TMEM
-// (bias + SiLU -> BF16 into the next padded buffer, including the circular
-// halo copies), pool the last layer and keep the per-parent FP64 energy
-// sums; warp 8 allocates TMEM and one lane issues every MMA and the
-// per-layer weight bulk copies (a two-deep ring).  Two slabs alternate so
-// the epilogue of one overlaps the MMAs of the other.  Every mbarrier wait
-// is bounded by a time budget; on expiry the CTA raises VMC_ERR_TIMEOUT,
-// drains its own copies and MMAs, frees TMEM and returns.
+// Warp roles: warps 0-15 (the "epilogue" group) build neighbours, drain
+// TMEM tile by tile (shift-add, bias, SiLU -> 16-bit into the next padded
+// buffer with the circular halo copies), pool the last layer and keep the
+// per-parent FP64 energy sums; warp 16 allocates TMEM and one lane issues
+// every MMA and the per-layer weight bulk copies (a two-deep ring).
+// Accumulators live in a ring of TMEM slots (one tile each) with full/empty
+// mbarriers, and two slabs alternate, so the epilogue of one tile overlaps
+// the MMAs of the next.  Every mbarrier wait is bounded by a time budget; on
+// expiry the CTA raises VMC_ERR_TIMEOUT, drains its own copies and MMAs,
+// frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <algorithm>
@@ -36,10 +42,14 @@
 namespace vmc {
 namespace tc {
 
-constexpr int NEPI = 256;       // epilogue threads (8 warps)
-constexpr int NTHREADS = 288;   // + MMA warp
-constexpr int MAX_SLOTS = 16;   // configurations per slab
-constexpr int RING = 32;        // parents in flight per CTA
+constexpr int NEPI_WARPS = 16;
+constexpr int NEPI = NEPI_WARPS * 32;     // epilogue threads
+constexpr int MMA_WARP = NEPI_WARPS;
+constexpr int NTHREADS = NEPI + 32;
+constexpr int MAX_SLOTS = 16;             // configurations per slab
+constexpr int RING = 32;                  // parents in flight per CTA
+constexpr int TS = 126;                   // tile stride in cells (128-row tiles overlap by 2)
+constexpr int MAX_TSLOTS = 16;            // TMEM accumulator slots
 constexpr int SMEM_LIMIT = 232448;
 
 struct Geo { int G, T, PW; };
@@ -55,8 +65,8 @@ struct Params {
     double J1, J2;
     const uint8_t *wimg;
     const float *bias32;
-    int S, Rcap, Tcap;
-    uint32_t tmem_cols;
+    int S, Rcap;
+    int nslots;                 // TMEM slots of 3 C columns
     Geo geo[17];
     double *out_a;
     int8_t *out_sign;
@@ -79,7 +89,8 @@ struct SlabMeta {
 };
 
 struct Ctrl {
-    uint64_t acc_full[2], act_ready[2], w_full[2], w_empty[2], drain;
+    uint64_t act_ready[2], w_full[2], w_empty[2], drain;
+    uint64_t t_full[MAX_TSLOTS], t_empty[MAX_TSLOTS];
     uint32_t tmem_base;
     int abort;
     int action, ok;
@@ -94,9 +105,11 @@ struct Ctrl {
     double slot_la[2][MAX_SLOTS];
     int slot_sg[2][MAX_SLOTS];
     Parent ring[RING];
+    float xch[2][4][4][3 * 8];  // [tile parity][channel group][lane quarter][x1(lane0), x2(lane0), x2(lane1)]
 };
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(2 + g) : "memory"); }
 
 // two FP32 values -> packed 16-bit pair (low half = a), round to nearest even
 template <bool F16>
@@ -111,17 +124,63 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
     }
 }
 
+// SiLU(z) = z / (1 + e^-z).  BF16 operands: z/2 (1 + tanh(z/2)) with the
+// hardware tanh (one MUFU op; its ~2^-11 error is below BF16 rounding for
+// the bulk of activations).  FP16 operands: e = exp(-|z|) (one MUFU op),
+// r = 1 / (1 + e) by Newton-Raphson from the linear estimate
+// 24/17 - 8/17 d on [1, 2] (relative error 1/17 -> (1/17)^4 after two
+// steps), sigmoid = r for z >= 0 and e r otherwise.
+template <bool F16>
+__device__ __forceinline__ float silu(float z)
+{
+    if constexpr (F16) {
+        const float e = __expf(-fabsf(z));
+        const float d = 1.0f + e;
+        float r = fmaf(-0.47058823529f, d, 1.41176470588f);
+        r = r * fmaf(-d, r, 2.0f);
+        r = r * fmaf(-d, r, 2.0f);
+        return z * (z >= 0.f ? r : e * r);
+    } else {
+        const float h = 0.5f * z;
+        return fmaf(h, tanh_approx(h), h);
+    }
+}
+
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
 {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
+__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b)
+{
+    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
 
 __device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
 
+template <int N>
+__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, float (&v)[N])
+{
+    if constexpr (N == 8) tmem_ld8(taddr, v);
+    else if constexpr (N == 16) tmem_ld16(taddr, v);
+    else {
+        static_assert(N == 4, "4, 8 or 16 columns");
+        uint32_t r[4];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+            : "r"(taddr)
+            : "memory");
+#pragma unroll
+        for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+    }
+}
+
 template <int C, bool F16>
 struct Kern {
-    static constexpr uint32_t WB = 9 * (C / 16) * 32 * C;   // bytes of one C -> C layer image
-    static constexpr int HALF = C / 2;                       // columns per epilogue thread
+    static constexpr uint32_t WB = 18 * C * C;    // bytes of one C -> C layer image
+    static constexpr int CPT = C / 4;             // channels per epilogue thread (4 channel groups)
+    static constexpr int NCOL = 3 * C;            // TMEM columns per tile slot
 
     const Params &p;
     uint8_t *smem;
@@ -141,50 +200,41 @@ struct Kern {
         return mbar_wait_bounded(bar, parity, &c.abort, p.budget_ns, &p.status->flags, &p.status->timeout_site, site);
     }
 
+    // A0 (embedding im2col) rows per plane for a slab of T tiles
+    __device__ static int a0_rows(int T) { return TS * (T - 1) + 128; }
+
     // ---------------------------------------------------------------- MMA
-    __device__ void issue_slab_layer(int s, int l, int bsel)
+    __device__ void issue_tile(int s, int l, int t, int bsel, uint32_t dcol)
     {
         const SlabMeta &m = c.slab[s];
-        const int T = m.T, PW = m.PW;
-        const uint32_t idesc = idesc_f16kind(128, C, F16);
         const uint32_t wb = smem_u32(smem + bsel * WB);
-        const uint32_t dcol0 = tmem + (uint32_t)(s * p.Tcap * C);
         if (l == 0) {
             const uint32_t a0 = smem_u32(act_buf(s, 1));
-            const uint64_t ad0 = smem_desc(a0, 128u * T * 16u, 128);
-            const uint64_t bdesc = smem_desc(wb, 16 * C, 128);
-            for (int t = 0; t < T; ++t)
-                umma_bf16(dcol0 + t * C, ad0 + (uint64_t)(t * 128), bdesc, idesc, 0);
+            const uint64_t ad = smem_desc(a0 + (uint32_t)(t * TS) * 16u, (uint32_t)a0_rows(m.T) * 16u, 128);
+            umma_bf16(dcol, ad, smem_desc(wb, 16 * C, 128), idesc_f16kind(128, C, F16), 0);
         } else {
-            // descriptors differ from the base only in the start-address
-            // field (16-byte units), so each MMA needs two integer adds
             const uint64_t ad0 = smem_desc(smem_u32(act_buf(s, (l - 1) & 1)), PS, 128);
-            const uint64_t bd0 = smem_desc(wb, 16 * C, 128);
+            const uint64_t bd0 = smem_desc(wb, 16 * NCOL, 128);
+            const uint32_t idesc = idesc_f16kind(128, NCOL, F16);
             const uint32_t plane2 = (2u * PS) >> 4;
-            for (int t = 0; t < T; ++t) {
-                const uint32_t d = dcol0 + t * C;
-                const uint32_t rt = (uint32_t)(t * 128);
+            const uint32_t rt = (uint32_t)(t * TS);
 #pragma unroll
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int ky = tap / 3, kx = tap - 3 * ky;
-                    const uint32_t roff = rt + (uint32_t)(ky * PW + kx);
+            for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                    for (int h = 0; h < C / 16; ++h)
-                        umma_bf16(d, ad0 + (uint64_t)(roff + h * plane2),
-                                  bd0 + (uint64_t)((tap * (C / 16) + h) * 2 * C), idesc, (tap | h) != 0);
-                }
-            }
+                for (int h = 0; h < C / 16; ++h)
+                    umma_bf16(dcol, ad0 + (uint64_t)(rt + (uint32_t)(ky * m.PW) + h * plane2),
+                              bd0 + (uint64_t)((ky * (C / 16) + h) * 2 * NCOL), idesc, (ky | h) != 0);
         }
     }
 
     __device__ void mma_role()
     {
-        const int D = p.D;
+        const int D = p.D, R = p.nslots;
         int issued[2] = {0, 0}, waited[2] = {0, 0};
         auto issue_w = [&](long long step) {
             const int bsel = (int)(step & 1);
             const int l = (int)(step % (D + 1));
-            const uint32_t bytes = (l == 0) ? 32u * C : WB;
+            const uint32_t bytes = (uint32_t)tc_layer_bytes(C, l);
             mbar_expect_tx(&c.w_full[bsel], bytes);
             bulk_g2s(smem + bsel * WB, p.wimg + tc_wimg_offset(C, l), bytes, &c.w_full[bsel]);
             issued[bsel]++;
@@ -194,12 +244,12 @@ struct Kern {
         bool dead[2] = {false, p.S < 2};
         int cnt[2] = {0, 0};
         uint32_t ph_ar[2] = {0, 0};
-        long long step = 0;
+        long long step = 0, gt = 0;   // weight step, global tile counter
         bool ok = true;
         while (ok && !(dead[0] && dead[1])) {
-            for (int l = 0; l <= D; ++l) {
+            for (int l = 0; l <= D && ok; ++l) {
                 bool any = false;
-                for (int s = 0; s < 2; ++s) {
+                for (int s = 0; s < 2 && ok; ++s) {
                     if (dead[s]) continue;
                     if (l == 0 || cnt[s] > 0) {
                         if (!wait_bar(&c.act_ready[s], ph_ar[s], 1)) { ok = false; break; }
@@ -215,35 +265,42 @@ struct Kern {
                         waited[bsel]++;
                         any = true;
                     }
-                    tc_fence_after();
-                    issue_slab_layer(s, l, (int)(step & 1));
-                    umma_commit(&c.acc_full[s]);
+                    const int T = *(volatile int *)&c.slab[s].T;
+                    for (int t = 0; t < T; ++t, ++gt) {
+                        const int slot = (int)(gt % R);
+                        const uint32_t par = (uint32_t)(((gt / R) & 1) ^ 1);
+                        if (!wait_bar(&c.t_empty[slot], par, 3)) { ok = false; break; }
+                        tc_fence_after();
+                        issue_tile(s, l, t, (int)(step & 1), tmem + (uint32_t)(slot * NCOL));
+                        umma_commit(&c.t_full[slot]);
+                    }
                 }
                 if (!ok || !any) break;
                 umma_commit(&c.w_empty[step & 1]);
                 if (step >= 1) {
-                    if (!wait_bar(&c.w_empty[(step - 1) & 1], (uint32_t)(((step - 1) >> 1) & 1), 3)) { ok = false; ++step; break; }
+                    if (!wait_bar(&c.w_empty[(step - 1) & 1], (uint32_t)(((step - 1) >> 1) & 1), 4)) { ok = false; break; }
                     issue_w(step + 1);
                 }
                 ++step;
             }
         }
-        // drain: every weight copy issued and every MMA committed must finish
+        // drain: every weight copy issued and every MMA issued must finish
         const long long cb = p.budget_ns > 1000000000LL ? p.budget_ns : 1000000000LL;
         int dummy_abort = 0;
         for (int bsel = 0; bsel < 2; ++bsel)
             while (waited[bsel] < issued[bsel]) {
                 if (!mbar_wait_bounded(&c.w_full[bsel], (uint32_t)(waited[bsel] & 1), &dummy_abort, cb,
-                                       &p.status->flags, &p.status->timeout_site, 4))
+                                       &p.status->flags, &p.status->timeout_site, 5))
                     break;
                 waited[bsel]++;
             }
-        umma_commit(&c.drain);   // completes once every MMA issued above has finished
-        mbar_wait_bounded(&c.drain, 0, &dummy_abort, cb, &p.status->flags, &p.status->timeout_site, 5);
+        umma_commit(&c.drain);
+        mbar_wait_bounded(&c.drain, 0, &dummy_abort, cb, &p.status->flags, &p.status->timeout_site, 6);
     }
 
-    // ---------------------------------------------------------------- epilogue
-    __device__ void row_coords(int r, const SlabMeta &m, int &y, int &j, int &x) const
+    // ---------------------------------------------------------------- epilogue helpers
+    // (y, j, x) of padded cell r; j = configuration slot, x column in it
+    __device__ __forceinline__ void cell_coords(int r, const SlabMeta &m, int &y, int &j, int &x) const
     {
         y = r / m.PW;
         const int X = r - y * m.PW;
@@ -251,100 +308,128 @@ struct Kern {
         x = X - j * (m.L + 2);
     }
 
-    __device__ void store_layer(int s, int l, int tid)
+    // Drain one tile: load the thread's CPT channels of P[q][kx C + co] for
+    // kx = 0 (and 1, 2 for C -> C layers), release the TMEM slot, and form
+    // z[q] = P0[q] + P1[q+1] + P2[q+2] across lanes.  Returns z (no bias).
+    __device__ void drain_tile(int l, int t, uint32_t slot_col, int tid, float (&z)[CPT])
+    {
+        const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + slot_col + (uint32_t)(g * CPT);
+        float x1[CPT], x2[CPT];
+        tmem_ld_n<CPT>(taddr, z);
+        if (l > 0) {
+            tmem_ld_n<CPT>(taddr + C, x1);
+            tmem_ld_n<CPT>(taddr + 2 * C, x2);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&c.t_empty[(slot_col / NCOL)]);
+        if (l == 0) return;
+        // rows q+1, q+2 of the next lane quarter, through shared memory
+        float *xo = c.xch[t & 1][g][wq];
+        if (wq > 0) {
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) { xo[i] = x1[i]; xo[CPT + i] = x2[i]; }
+            } else if (lane == 1) {
+#pragma unroll
+                for (int i = 0; i < CPT; ++i) xo[2 * CPT + i] = x2[i];
+            }
+        }
+        group_sync(g);
+        const float *xn = c.xch[t & 1][g][(wq + 1) & 3];
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            float a1 = __shfl_down_sync(0xffffffffu, x1[i], 1);
+            float a2 = __shfl_down_sync(0xffffffffu, x2[i], 2);
+            if (lane == 31) { a1 = xn[i]; a2 = xn[2 * CPT + i]; }
+            else if (lane == 30) { a2 = xn[CPT + i]; }
+            z[i] += a1 + a2;
+        }
+    }
+
+    // epilogue of one tile of a hidden layer: bias, SiLU, 16-bit, stores
+    __device__ void store_tile(int s, int l, int t, uint32_t slot_col, int tid)
     {
         const SlabMeta &m = c.slab[s];
         const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
-        const int L = m.L, PW = m.PW, count = m.count;
-        const uint32_t out = smem_u32(act_buf(s, l & 1));
-        const float *bias = p.bias32 + l * C + g * HALF;
-        float bb[HALF];
+        float z[CPT];
+        drain_tile(l, t, slot_col, tid, z);
+        const int i_row = wq * 32 + lane;
+        const int r = t * TS + i_row;
+        int y, j, x;
+        cell_coords(r, m, y, j, x);
+        const int L = m.L, PW = m.PW;
+        if (i_row < TS && y < L && x < L && j < m.count) {
+            const float *bias = p.bias32 + l * C + g * CPT;
+            uint32_t w[CPT / 2];
 #pragma unroll
-        for (int i = 0; i < HALF; ++i) bb[i] = __ldg(bias + i);
-        for (int t = 0; t < m.T; ++t) {
-            const int r = t * 128 + wq * 32 + lane;
-            const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(s * p.Tcap * C + t * C + g * HALF);
-            float v[HALF];
-            if constexpr (HALF == 16) tmem_ld16(taddr, v); else tmem_ld8(taddr, v);
-            int y, j, x;
-            row_coords(r, m, y, j, x);
-            if (y < L && x < L && j < count) {
-                uint32_t w[HALF / 2];
-#pragma unroll
-                for (int i = 0; i < HALF / 2; ++i) {
-                    const float h0 = 0.5f * (v[2 * i] + bb[2 * i]), h1 = 0.5f * (v[2 * i + 1] + bb[2 * i + 1]);
-                    const float a0 = fmaf(h0, tanh_approx(h0), h0);   // SiLU(z) = (z/2)(1 + tanh(z/2))
-                    const float a1 = fmaf(h1, tanh_approx(h1), h1);
-                    w[i] = pack2<F16>(a0, a1);
-                }
-                const int R0 = (y + 1) * PW + j * (L + 2) + x + 1;
-                int rows[4];
-                int nr = 1;
-                rows[0] = R0;
-                const int hx = (x == 0) ? L : ((x == L - 1) ? -L : 0);
-                const int vy = (y == 0) ? L * PW : ((y == L - 1) ? -L * PW : 0);
-                if (hx) rows[nr++] = R0 + hx;
-                if (vy) {
-                    rows[nr++] = R0 + vy;
-                    if (hx) rows[nr++] = R0 + vy + hx;
-                }
-                for (int q = 0; q < nr; ++q) {
-                    const uint32_t a = out + (uint32_t)rows[q] * 16u;
-                    if constexpr (HALF == 16) {
-                        st_shared_v4(a + (2 * g) * PS, w[0], w[1], w[2], w[3]);
-                        st_shared_v4(a + (2 * g + 1) * PS, w[4], w[5], w[6], w[7]);
-                    } else {
-                        st_shared_v4(a + g * PS, w[0], w[1], w[2], w[3]);
-                    }
-                }
+            for (int i = 0; i < CPT / 2; ++i)
+                w[i] = pack2<F16>(silu<F16>(z[2 * i] + __ldg(bias + 2 * i)), silu<F16>(z[2 * i + 1] + __ldg(bias + 2 * i + 1)));
+            const int R0 = (y + 1) * PW + j * (L + 2) + x + 1;
+            const int hx = (x == 0) ? L : ((x == L - 1) ? -L : 0);
+            const int vy = (y == 0) ? L * PW : ((y == L - 1) ? -L * PW : 0);
+            int rows[4];
+            int nr = 1;
+            rows[0] = R0;
+            if (hx) rows[nr++] = R0 + hx;
+            if (vy) {
+                rows[nr++] = R0 + vy;
+                if (hx) rows[nr++] = R0 + vy + hx;
+            }
+            const uint32_t out = smem_u32(act_buf(s, l & 1));
+            // channel group g: C = 32 -> plane g (8 channels, 16 B);
+            //                  C = 16 -> plane g/2, half (g & 1) (4 channels, 8 B)
+            for (int q = 0; q < nr; ++q) {
+                const uint32_t a = out + (uint32_t)rows[q] * 16u;
+                if constexpr (CPT == 8) st_shared_v4(a + g * PS, w[0], w[1], w[2], w[3]);
+                else st_shared_v2(a + (g >> 1) * PS + (g & 1) * 8u, w[0], w[1]);
             }
         }
     }
 
-    __device__ void pool(int s, int tid)
+    // epilogue of one tile of the last layer: pooling partials
+    __device__ void pool_tile(int s, int t, uint32_t slot_col, int tid, float *partF, int *partI, int rows)
+    {
+        const SlabMeta &m = c.slab[s];
+        const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
+        float z[CPT];
+        drain_tile(p.D, t, slot_col, tid, z);
+        const int i_row = wq * 32 + lane;
+        const int r = t * TS + i_row;
+        int y, j, x;
+        cell_coords(r, m, y, j, x);
+        if (i_row < TS && y < m.L && x < m.L && j < m.count) {
+            const float *bias = p.bias32 + p.D * C + g * CPT;
+            float sl = 0.f;
+            int neg = 0, zer = 0;
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                const float v = z[i] + __ldg(bias + i);
+                sl += __log2f(fabsf(v));
+                neg += (v < 0.f);
+                zer += (v == 0.f);
+            }
+            partF[g * rows + r] = sl;
+            partI[g * rows + r] = neg | (zer << 16);
+        }
+    }
+
+    // per-configuration FP64 sums and the per-parent bookkeeping
+    __device__ void pool_finish(int s, int tid, const float *partF, const int *partI, int rows)
     {
         SlabMeta &m = c.slab[s];
-        const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
-        const int L = m.L, count = m.count, rows = 128 * m.T;
-        float *partF = reinterpret_cast<float *>(act_buf(s, (p.D - 1) & 1));
-        int *partI = reinterpret_cast<int *>(partF + 2 * rows);
-        const float *bias = p.bias32 + p.D * C + g * HALF;
-        float bb[HALF];
-#pragma unroll
-        for (int i = 0; i < HALF; ++i) bb[i] = __ldg(bias + i);
-        for (int t = 0; t < m.T; ++t) {
-            const int r = t * 128 + wq * 32 + lane;
-            const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(s * p.Tcap * C + t * C + g * HALF);
-            float v[HALF];
-            if constexpr (HALF == 16) tmem_ld16(taddr, v); else tmem_ld8(taddr, v);
-            int y, j, x;
-            row_coords(r, m, y, j, x);
-            if (y < L && x < L && j < count) {
-                float sl = 0.f;
-                int neg = 0, zer = 0;
-#pragma unroll
-                for (int i = 0; i < HALF; ++i) {
-                    const float z = v[i] + bb[i];
-                    sl += __log2f(fabsf(z));
-                    neg += (z < 0.f);
-                    zer += (z == 0.f);
-                }
-                partF[g * rows + r] = sl;
-                partI[g * rows + r] = neg | (zer << 16);
-            }
-        }
-        epi_sync();
-        // deterministic FP64 sum per configuration
-        for (int j = warp; j < count; j += 8) {
+        const int warp = tid >> 5, lane = tid & 31;
+        const int L = m.L, count = m.count, npix = L * L;
+        for (int j = warp; j < count; j += NEPI_WARPS) {
             double acc = 0.0;
             int neg = 0, zer = 0;
-            const int npix = L * L;
-            for (int idx = lane; idx < 2 * npix; idx += 32) {
-                const int hh = idx / npix, pix = idx - hh * npix;
+            for (int idx = lane; idx < 4 * npix; idx += 32) {
+                const int gg = idx / npix, pix = idx - gg * npix;
                 const int y = pix / L, x = pix - y * L;
                 const int r = y * m.PW + j * (L + 2) + x;
-                acc += (double)partF[hh * rows + r];
-                const int nz = partI[hh * rows + r];
+                acc += (double)partF[gg * rows + r];
+                const int nz = partI[gg * rows + r];
                 neg += nz & 0xffff;
                 zer += nz >> 16;
             }
@@ -405,13 +490,14 @@ struct Kern {
     }
 
     // Build the embedding-layer im2col rows of slots [first, first+n):
-    // nine spins of sigma' around each cell, 16 BF16 per row in two planes.
+    // nine spins of sigma' around each cell, 16 values per row in two planes.
     __device__ void build_rows(int s, int first, int n, int tid)
     {
         const SlabMeta &m = c.slab[s];
         const int L = m.L, PW = m.PW, npix = L * L;
         const uint32_t a0 = smem_u32(act_buf(s, 1));
-        const uint32_t plane = 128u * m.T * 16u;
+        const uint32_t plane = (uint32_t)a0_rows(m.T) * 16u;
+        const uint32_t up = F16 ? 0x3C00u : 0x3F80u, dn = F16 ? 0xBC00u : 0xBF80u;
         for (int idx = tid; idx < n * npix; idx += NEPI) {
             const int jj = first + idx / npix, pix = idx - (idx / npix) * npix;
             const int y = pix / L, x = pix - y * L;
@@ -431,7 +517,7 @@ struct Kern {
                     int v = spins[site];
                     if (site == bi) v = spins[bj];
                     else if (site == bj) v = spins[bi];
-                    h[ky * 3 + kx] = F16 ? (v > 0 ? 0x3C00u : 0xBC00u) : (v > 0 ? 0x3F80u : 0xBF80u);
+                    h[ky * 3 + kx] = v > 0 ? up : dn;
                 }
             }
             const uint32_t q = (uint32_t)(y * PW + jj * (L + 2) + x) * 16u;
@@ -493,7 +579,7 @@ struct Kern {
                     const int r = c.ring_head;
                     c.ring_head = (r + 1) % RING;
                     Parent &P = c.ring[r];
-                    if (P.valid) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); }   // cannot happen: RING > parents in flight
+                    if (P.valid) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); }
                     P.b = b;
                     P.diag = (p.mode == 1) ? diag_energy(Lb, c.nb_a1, c.nb_a2, p.J1, p.J2) : 0.0;
                     P.la0 = 0.0; P.acc = 0.0; P.sg0 = 0;
@@ -539,12 +625,12 @@ struct Kern {
         const int count = m.count;
         if (count > 0) {
             // rows that belong to no configuration: zero (finite) input
-            const int L = m.L, rows = 128 * m.T;
+            const int L = m.L, rows = a0_rows(m.T);
             const uint32_t a0 = smem_u32(act_buf(s, 1));
             const uint32_t plane = (uint32_t)rows * 16u;
             for (int r = tid; r < rows; r += NEPI) {
                 int y, j, x;
-                row_coords(r, m, y, j, x);
+                cell_coords(r, m, y, j, x);
                 if (!(y < L && x < L && j < count)) {
                     st_shared_v4(a0 + r * 16u, 0u, 0u, 0u, 0u);
                     st_shared_v4(a0 + plane + r * 16u, 0u, 0u, 0u, 0u);
@@ -557,16 +643,26 @@ struct Kern {
     __device__ void signal_ready(int s, int tid)
     {
         fence_proxy_async_smem();
-        tc_fence_before();
         epi_sync();
         if (tid == 0) mbar_arrive(&c.act_ready[s]);
     }
 
+    // wait (one thread) for the accumulator slot of tile gt, broadcast the result
+    __device__ bool wait_tile(long long gt, int tid)
+    {
+        const int R = p.nslots;
+        if (tid == 0) c.ok = wait_bar(&c.t_full[gt % R], (uint32_t)((gt / R) & 1), 7) ? 1 : 0;
+        epi_sync();
+        const bool ok = c.ok != 0;
+        if (ok) tc_fence_after();
+        return ok;
+    }
+
     __device__ void epilogue_role(int tid)
     {
-        const int D = p.D;
+        const int D = p.D, R = p.nslots;
         bool dead[2] = {false, true};
-        uint32_t ph_af[2] = {0, 0};
+        long long gt = 0;
         for (int s = 0; s < p.S; ++s) {
             const int cnt = fill(s, tid);
             signal_ready(s, tid);
@@ -576,16 +672,23 @@ struct Kern {
             for (int l = 0; l <= D; ++l) {
                 for (int s = 0; s < 2; ++s) {
                     if (dead[s]) continue;
-                    if (tid == 0) c.ok = wait_bar(&c.acc_full[s], ph_af[s], 6) ? 1 : 0;
-                    epi_sync();
-                    if (!c.ok) return;
-                    ph_af[s] ^= 1;
-                    tc_fence_after();
+                    const int T = c.slab[s].T;
                     if (l < D) {
-                        store_layer(s, l, tid);
+                        for (int t = 0; t < T; ++t, ++gt) {
+                            if (!wait_tile(gt, tid)) return;
+                            store_tile(s, l, t, (uint32_t)((gt % R) * NCOL), tid);
+                        }
                         signal_ready(s, tid);
                     } else {
-                        pool(s, tid);
+                        const int rows = TS * T;
+                        float *partF = reinterpret_cast<float *>(act_buf(s, (p.D - 1) & 1));
+                        int *partI = reinterpret_cast<int *>(partF + 4 * rows);
+                        for (int t = 0; t < T; ++t, ++gt) {
+                            if (!wait_tile(gt, tid)) return;
+                            pool_tile(s, t, (uint32_t)((gt % R) * NCOL), tid, partF, partI, rows);
+                        }
+                        epi_sync();
+                        pool_finish(s, tid, partF, partI, rows);
                         const int cnt = fill(s, tid);
                         signal_ready(s, tid);
                         dead[s] = (cnt == 0);
@@ -607,10 +710,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     uint16_t *list = reinterpret_cast<uint16_t *>(spins + ((p.L_max * p.L_max + 15) & ~15));
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&c.acc_full[i], 1);
             mbar_init(&c.act_ready[i], 1);
             mbar_init(&c.w_full[i], 1);
             mbar_init(&c.w_empty[i], 1);
+        }
+        for (int i = 0; i < MAX_TSLOTS; ++i) {
+            mbar_init(&c.t_full[i], 1);
+            mbar_init(&c.t_empty[i], NEPI_WARPS);
         }
         mbar_init(&c.drain, 1);
         c.abort = 0;
@@ -621,19 +727,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
         mbar_fence_init();
         fence_proxy_async_smem();
     }
-    if (warp == 8) tmem_alloc(&c.tmem_base, p.tmem_cols);
+    if (warp == MMA_WARP) tmem_alloc(&c.tmem_base, 512);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     Kern<C, F16> k(p, smem, c, spins, list, BUF, c.tmem_base);
-    if (warp < 8) k.epilogue_role(tid);
+    if (warp < MMA_WARP) k.epilogue_role(tid);
     else if ((tid & 31) == 0) k.mma_role();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) {
+    if (warp == MMA_WARP) {
         __syncwarp();
-        tmem_dealloc(c.tmem_base, p.tmem_cols);
+        tmem_dealloc(c.tmem_base, 512);
     }
 }
 
@@ -644,81 +750,71 @@ static size_t ctrl_bytes(int L_max)
     return sizeof(Ctrl) + ((L_max * L_max + 15) & ~15) + (size_t)4 * L_max * L_max * 2 + 64;
 }
 
+// tiles and shared-memory rows (per plane) of a slab of G lattices of side L
 static int rows_needed(int L, int G, int *T_out)
 {
     const int PW = G * (L + 2);
-    const int T = (L * PW + 127) / 128;
+    const int T = (L * PW + TS - 1) / TS;
     *T_out = T;
-    return std::max((L + 2) * PW, 128 * T + 2 * PW + 2);
+    const int mma_rows = TS * (T - 1) + 128 + 2 * PW;   // last A row any MMA of the slab reads, + 1
+    return (std::max((L + 2) * PW, mma_rows) + 7) & ~7;
 }
 
 struct Plan {
-    int S, Rcap, Tcap;
-    uint32_t tmem_cols;
+    int S, Rcap;
     Geo geo[17];
     size_t smem;
 };
 
-// Largest-efficiency G for lattice L under the row / TMEM capacity.
-static Geo best_geo(int L, int C, int S, int Rcap, int Tcap, int Gwant)
+// Largest-efficiency G for lattice L under the row capacity.
+static Geo best_geo(int L, int Rcap, int Gwant)
 {
     Geo best{0, 0, 0};
     double be = -1.0;
     for (int G = 1; G <= MAX_SLOTS; ++G) {
         int T;
         const int R = rows_needed(L, G, &T);
-        if (R > Rcap || T > Tcap) break;
-        const double eff = (double)L * L * G / (128.0 * T);
+        if (R > Rcap) break;
+        const double eff = (double)L * L * G / (double)(TS * T);
         if (Gwant > 0) {
             if (G == Gwant) { best = Geo{G, T, G * (L + 2)}; be = eff; }
             continue;
         }
         if (eff > be + 1e-9) { be = eff; best = Geo{G, T, G * (L + 2)}; }
     }
-    (void)C; (void)S;
     return best;
 }
 
 static int make_plan(const vmc_ctx *ctx, int L_main, int L_max, bool ragged, Plan *pl)
 {
-    const int C = ctx->arch.channels, D = ctx->arch.n_layers_cc;
-    (void)D;
+    const int C = ctx->arch.channels;
     TileChoice tc;
     auto it = ctx->tiles.find(L_main);
     if (it != ctx->tiles.end()) tc = it->second;
     const int S = tc.slabs ? tc.slabs : 2;
-    const size_t wb = 2 * (size_t)(9 * (C / 16) * 32 * C);
+    const size_t wb = 2 * (size_t)(18 * C * C);
     const size_t ctrl = ctrl_bytes(L_max);
     const size_t avail = SMEM_LIMIT - wb - ctrl - 1024;
-    // row capacity of one plane from shared memory, tile capacity from TMEM
-    int Rcap = (int)(avail / ((size_t)2 * S * (C / 8) * 16));
-    int Tcap = 512 / (S * C);
-    // For a uniform batch size the buffers to the chosen geometry.
-    Geo gmain = best_geo(L_main, C, S, Rcap, Tcap, tc.slab_configs);
+    int Rcap = (int)(avail / ((size_t)2 * S * (C / 8) * 16)) & ~7;
+    Geo gmain = best_geo(L_main, Rcap, tc.slab_configs);
     if (gmain.G == 0) return VMC_ERR_UNSUPPORTED;
     if (!ragged) {
         int T;
         Rcap = rows_needed(L_main, gmain.G, &T);
-        Tcap = T;
     }
     pl->S = S;
     pl->Rcap = Rcap;
-    pl->Tcap = Tcap;
     for (int i = 0; i < 17; ++i) pl->geo[i] = Geo{0, 0, 0};
     if (ragged) {
         for (int L = 4; L <= L_max; L += 2) {
             TileChoice tl;
             auto jt = ctx->tiles.find(L);
             if (jt != ctx->tiles.end()) tl = jt->second;
-            pl->geo[L >> 1] = best_geo(L, C, S, Rcap, Tcap, tl.slab_configs);
+            pl->geo[L >> 1] = best_geo(L, Rcap, tl.slab_configs);
         }
     } else {
         pl->geo[L_main >> 1] = gmain;
     }
-    uint32_t cols = 32;
-    while (cols < (uint32_t)(S * Tcap * C)) cols <<= 1;
-    if (cols > 512) return VMC_ERR_UNSUPPORTED;
-    pl->tmem_cols = cols;
     pl->smem = wb + (size_t)2 * S * (C / 8) * Rcap * 16 + ctrl;
     if (pl->smem < 120 * 1024) pl->smem = 120 * 1024;   // keeps one CTA (and one TMEM owner) per SM
     if (pl->smem > SMEM_LIMIT) return VMC_ERR_UNSUPPORTED;
@@ -728,7 +824,7 @@ static int make_plan(const vmc_ctx *ctx, int L_main, int L_max, bool ragged, Pla
 template <int C, bool F16>
 static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, const int64_t *offs,
                   const int32_t *Ls, int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr,
-                  cudaStream_t st, int grid_override)
+                  cudaStream_t st)
 {
     Params p;
     p.mode = mode; p.B = B; p.sigma = sigma; p.offs = offs; p.Ls = Ls;
@@ -737,7 +833,8 @@ static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, c
     p.J1 = ctx->J1; p.J2 = ctx->J2;
     p.wimg = reinterpret_cast<const uint8_t *>(ctx->wimg);
     p.bias32 = ctx->bias32;
-    p.S = pl.S; p.Rcap = pl.Rcap; p.Tcap = pl.Tcap; p.tmem_cols = pl.tmem_cols;
+    p.S = pl.S; p.Rcap = pl.Rcap;
+    p.nslots = std::min(MAX_TSLOTS, 512 / (3 * C));
     for (int i = 0; i < 17; ++i) p.geo[i] = pl.geo[i];
     p.out_a = out_a; p.out_sign = static_cast<int8_t *>(out_b); p.n_nbr = n_nbr;
     p.status = ctx->status; p.counter = ctx->counter;
@@ -747,7 +844,7 @@ static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, c
     if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "cudaFuncSetAttribute(tc_eloc)");
     e = cudaMemsetAsync(ctx->counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "counter reset");
-    int grid = grid_override > 0 ? grid_override : ctx->sm_count;
+    int grid = ctx->sm_count;
     if ((int64_t)grid > B) grid = (int)B;
     kfn<<<grid, NTHREADS, pl.smem, st>>>(p);
     ctx->launches += 1;
@@ -760,10 +857,10 @@ static int launch_any(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigm
 {
     const bool f16 = ctx->arch.precision == VMC_FP16;
     if (ctx->arch.channels == 32)
-        return f16 ? launch<32, true>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st, 0)
-                   : launch<32, false>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st, 0);
-    return f16 ? launch<16, true>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st, 0)
-               : launch<16, false>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st, 0);
+        return f16 ? launch<32, true>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st)
+                   : launch<32, false>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st);
+    return f16 ? launch<16, true>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st)
+               : launch<16, false>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st);
 }
 
 // ------------------------------------------------------------------ diagnostics
@@ -793,7 +890,7 @@ __global__ void umma_selftest_kernel(const uint16_t *A, const uint16_t *Bm, floa
     }
     if (tid == 0) { mbar_init(&bar, 1); mbar_fence_init(); }
     fence_proxy_async_smem();
-    if (warp == 0) tmem_alloc(&tbase, 64);
+    if (warp == 0) tmem_alloc(&tbase, 128);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -821,7 +918,7 @@ __global__ void umma_selftest_kernel(const uint16_t *A, const uint16_t *Bm, floa
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tbase, 64);
+    if (warp == 0) tmem_dealloc(tbase, 128);
 }
 
 __global__ void wait_timeout_kernel(DevStatus *st, long long budget)
@@ -892,7 +989,7 @@ extern "C" int vmc_debug_umma_selftest(const uint16_t *A_dev, const uint16_t *B_
                                        int shift, int variant, void *stream)
 {
     if (!A_dev || !B_dev || !D_dev) return VMC_ERR_ARG;
-    if (N < 16 || N > 64 || N % 16 || K < 16 || K > 64 || K % 16 || shift < 0 || shift > 64) return VMC_ERR_ARG;
+    if (N < 16 || N > 128 || N % 16 || K < 16 || K > 32 || K % 16 || shift < 0 || shift > 64) return VMC_ERR_ARG;
     int dev = 0, maj = 0, mnr = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);

@@ -1,37 +1,41 @@
-// Shared-memory operand layouts of the tcgen05 (BF16) convolution path.
+// Shared-memory operand layouts of the tcgen05 convolution path.
 //
 // Both MMA operands are K-major without swizzle: a "core matrix" is 8 rows
-// of 16 bytes (8 BF16 values along K) stored contiguously (128 B).
+// of 16 bytes (8 16-bit values along K) stored contiguously (128 B).
 //  - A (activations): one "plane" per group of 8 channels; a plane is a
 //    column of 16-byte rows, one row per padded lattice cell, so core
 //    matrices adjacent in M are 128 B apart (SBO = 128) and the two K-groups
 //    of one MMA (16 channels) are one plane apart (LBO = plane stride).
-//    Row r + s of the same plane is r's address + 16 s, so the 3x3 tap
-//    shift of the implicit GEMM is a plain change of the start address.
-//  - B (weights): per K-chunk of 16, C output-channel rows: the C/8 core
-//    matrices of K-group 0, then those of K-group 1 (SBO = 128,
-//    LBO = 16 C bytes); 32 C bytes per chunk.
-//    Embedding layer (c_in = 1): one chunk, K = tap (9 used, 7 zero).
-//    C -> C layer: 9 (C/16) chunks, chunk = tap * (C/16) + h, K = input
-//    channel 16 h + k.
+//    Row r + s of the same plane is r's address + 16 s, so the vertical tap
+//    shift ky * PW of the implicit GEMM is a plain change of start address.
+//  - B (weights): per K-chunk of 16, N rows: the N/8 core matrices of
+//    K-group 0, then those of K-group 1 (SBO = 128, LBO = 16 N); 32 N bytes
+//    per chunk.
+//    Embedding layer (c_in = 1): one chunk, N = C, K = tap (9 used, 7 zero).
+//    C -> C layer: the three horizontal taps share an MMA, N = 3 C with
+//    n = kx * C + co; 3 (C/16) chunks, chunk = ky * (C/16) + h, K = input
+//    channel 16 h + k.  The accumulator column kx * C + co of row q then
+//    holds the kx-tap partial of output cell q - kx, which the epilogue
+//    adds across TMEM lanes.
 #pragma once
 #include <stdint.h>
 
 namespace vmc {
 
-__host__ __device__ __forceinline__ int64_t tc_chunk_bytes(int C) { return 32LL * C; }
-__host__ __device__ __forceinline__ int tc_chunks(int C, int l) { return l == 0 ? 1 : 9 * (C / 16); }
-__host__ __device__ __forceinline__ int64_t tc_layer_bytes(int C, int l) { return tc_chunks(C, l) * tc_chunk_bytes(C); }
+__host__ __device__ __forceinline__ int tc_chunk_n(int C, int l) { return l == 0 ? C : 3 * C; }
+__host__ __device__ __forceinline__ int64_t tc_chunk_bytes(int C, int l) { return 32LL * tc_chunk_n(C, l); }
+__host__ __device__ __forceinline__ int tc_chunks(int C, int l) { return l == 0 ? 1 : 3 * (C / 16); }
+__host__ __device__ __forceinline__ int64_t tc_layer_bytes(int C, int l) { return tc_chunks(C, l) * tc_chunk_bytes(C, l); }
 __host__ __device__ __forceinline__ int64_t tc_wimg_offset(int C, int l)
 {
-    return l == 0 ? 0 : tc_chunk_bytes(C) + (int64_t)(l - 1) * tc_layer_bytes(C, 1);
+    return l == 0 ? 0 : tc_layer_bytes(C, 0) + (int64_t)(l - 1) * tc_layer_bytes(C, 1);
 }
 __host__ __device__ __forceinline__ int64_t tc_wimg_bytes(int C, int D) { return tc_wimg_offset(C, D + 1); }
 
-// byte offset of element (n, k) inside one B chunk
-__host__ __device__ __forceinline__ int tc_b_elem_offset(int C, int n, int k)
+// byte offset of element (n, k) inside one B chunk with N rows
+__host__ __device__ __forceinline__ int tc_b_elem_offset(int N, int n, int k)
 {
-    return (k >> 3) * (16 * C) + (n >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+    return (k >> 3) * (16 * N) + (n >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
 }
 
 }  // namespace vmc

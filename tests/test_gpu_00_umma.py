@@ -10,7 +10,8 @@ from paper_2108_13830_gb300.binding import umma_selftest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("N,K,shift", [(32, 32, 0), (32, 32, 5), (16, 32, 3), (32, 16, 0), (16, 16, 37)])
+@pytest.mark.parametrize("N,K,shift", [(32, 32, 0), (32, 32, 5), (16, 32, 3), (32, 16, 0), (16, 16, 37),
+                                     (96, 32, 7), (48, 16, 2), (128, 32, 0)])
 def test_umma_tile(N, K, shift):
     g = torch.Generator().manual_seed(N * 100 + K + shift)
     A = torch.randn(128 + shift, K, generator=g).bfloat16().cuda()
