@@ -84,6 +84,7 @@ struct Parent {
 
 struct SlabMeta {
     int count, L, G, T, PW;
+    uint32_t mPW, mLP;          // floor(2^32 / PW) + 1, floor(2^32 / (L+2)) + 1: r / PW = umulhi(r, mPW)
     int parent[MAX_SLOTS];
     int bond[MAX_SLOTS];
 };
@@ -94,6 +95,7 @@ struct Ctrl {
     uint32_t tmem_base;
     int abort;
     int action, ok;
+    int okf[2];                 // abort snapshots, indexed by the parity of the check
     long long new_b;
     int new_L;
     int cur_parent, cur_k, cur_nlist, cur_L;
@@ -300,30 +302,35 @@ struct Kern {
 
     // ---------------------------------------------------------------- epilogue helpers
     // (y, j, x) of padded cell r; j = configuration slot, x column in it
+    // (exact for r < 2^16 and divisors < 2^10: umulhi(r, floor(2^32/d) + 1) = floor(r/d))
     __device__ __forceinline__ void cell_coords(int r, const SlabMeta &m, int &y, int &j, int &x) const
     {
-        y = r / m.PW;
+        y = (int)__umulhi((uint32_t)r, m.mPW);
         const int X = r - y * m.PW;
-        j = X / (m.L + 2);
+        j = (int)__umulhi((uint32_t)X, m.mLP);
         x = X - j * (m.L + 2);
     }
 
     // Drain one tile: load the thread's CPT channels of P[q][kx C + co] for
     // kx = 0 (and 1, 2 for C -> C layers), release the TMEM slot, and form
     // z[q] = P0[q] + P1[q+1] + P2[q+2] across lanes.  Returns z (no bias).
-    __device__ void drain_tile(int l, int t, uint32_t slot_col, int tid, float (&z)[CPT])
+    __device__ void drain_tile(int l, int t, uint32_t slot_col, int tid, float (&z)[CPT], bool ok)
     {
         const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
         const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + slot_col + (uint32_t)(g * CPT);
         float x1[CPT], x2[CPT];
-        tmem_ld_n<CPT>(taddr, z);
-        if (l > 0) {
-            tmem_ld_n<CPT>(taddr + C, x1);
-            tmem_ld_n<CPT>(taddr + 2 * C, x2);
+        if (!ok) {
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) { z[i] = 0.f; x1[i] = 0.f; x2[i] = 0.f; }
+        } else if (l > 0) {
+            if constexpr (CPT == 8) tmem_ld8x3(taddr, C, z, x1, x2);
+            else tmem_ld4x3(taddr, C, z, x1, x2);
+        } else {
+            tmem_ld_n<CPT>(taddr, z);
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&c.t_empty[(slot_col / NCOL)]);
+        if (ok && lane == 0) mbar_arrive(&c.t_empty[(slot_col / NCOL)]);
         if (l == 0) return;
         // rows q+1, q+2 of the next lane quarter, through shared memory
         float *xo = c.xch[t & 1][g][wq];
@@ -349,12 +356,13 @@ struct Kern {
     }
 
     // epilogue of one tile of a hidden layer: bias, SiLU, 16-bit, stores
-    __device__ void store_tile(int s, int l, int t, uint32_t slot_col, int tid)
+    __device__ void store_tile(int s, int l, int t, uint32_t slot_col, int tid, bool ok)
     {
         const SlabMeta &m = c.slab[s];
         const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
         float z[CPT];
-        drain_tile(l, t, slot_col, tid, z);
+        drain_tile(l, t, slot_col, tid, z, ok);
+        if (!ok) return;
         const int i_row = wq * 32 + lane;
         const int r = t * TS + i_row;
         int y, j, x;
@@ -389,12 +397,13 @@ struct Kern {
     }
 
     // epilogue of one tile of the last layer: pooling partials
-    __device__ void pool_tile(int s, int t, uint32_t slot_col, int tid, float *partF, int *partI, int rows)
+    __device__ void pool_tile(int s, int t, uint32_t slot_col, int tid, float *partF, int *partI, int rows, bool ok)
     {
         const SlabMeta &m = c.slab[s];
         const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
         float z[CPT];
-        drain_tile(p.D, t, slot_col, tid, z);
+        drain_tile(p.D, t, slot_col, tid, z, ok);
+        if (!ok) return;
         const int i_row = wq * 32 + lane;
         const int r = t * TS + i_row;
         int y, j, x;
@@ -535,7 +544,9 @@ struct Kern {
         for (;;) {
             if (tid == 0) {
                 int act = 2;
-                if (c.cur_parent >= 0 && c.cur_k <= c.cur_nlist) {
+                if (c.abort) {
+                    act = 2;   // stop filling; the caller's next abort check ends the epilogue
+                } else if (c.cur_parent >= 0 && c.cur_k <= c.cur_nlist) {
                     act = 0;
                 } else {
                     while (!c.no_more) {
@@ -604,6 +615,8 @@ struct Kern {
                     m.G = p.geo[Lc >> 1].G;
                     m.T = p.geo[Lc >> 1].T;
                     m.PW = p.geo[Lc >> 1].PW;
+                    m.mPW = (uint32_t)(0xFFFFFFFFu / (uint32_t)m.PW) + 1u;
+                    m.mLP = (uint32_t)(0xFFFFFFFFu / (uint32_t)(Lc + 2)) + 1u;
                 }
                 if (m.G < 1 || m.G > MAX_SLOTS) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); m.G = 1; }
                 const int n_take = min(m.G - m.count, c.cur_nlist + 1 - c.cur_k);
@@ -620,7 +633,7 @@ struct Kern {
             epi_sync();
             build_rows(s, c.seg_first, c.seg_n, tid);
             epi_sync();
-            if (m.count >= m.G || c.abort) break;
+            if (m.count >= m.G) break;
         }
         const int count = m.count;
         if (count > 0) {
@@ -647,15 +660,18 @@ struct Kern {
         if (tid == 0) mbar_arrive(&c.act_ready[s]);
     }
 
-    // wait (one thread) for the accumulator slot of tile gt, broadcast the result
+    // Each warp waits (one lane, bounded) for the accumulator slot of tile
+    // gt.  A warp whose wait fails keeps going through the tile loop without
+    // touching TMEM, so every named barrier still sees all participants; the
+    // whole epilogue returns together at the next CTA-wide check of c.abort.
     __device__ bool wait_tile(long long gt, int tid)
     {
         const int R = p.nslots;
-        if (tid == 0) c.ok = wait_bar(&c.t_full[gt % R], (uint32_t)((gt / R) & 1), 7) ? 1 : 0;
-        epi_sync();
-        const bool ok = c.ok != 0;
+        int ok = 0;
+        if ((tid & 31) == 0) ok = wait_bar(&c.t_full[gt % R], (uint32_t)((gt / R) & 1), 7) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
         if (ok) tc_fence_after();
-        return ok;
+        return ok != 0;
     }
 
     __device__ void epilogue_role(int tid)
@@ -663,6 +679,16 @@ struct Kern {
         const int D = p.D, R = p.nslots;
         bool dead[2] = {false, true};
         long long gt = 0;
+        int nchk = 0;
+        // CTA-wide abort check: tid 0 snapshots c.abort into okf[parity]; the
+        // next write to the same slot comes two barriers later, after every
+        // thread has read this one
+        auto go_on = [&]() {
+            const int k = (nchk++) & 1;
+            if (tid == 0) c.okf[k] = c.abort ? 0 : 1;
+            epi_sync();
+            return c.okf[k] != 0;
+        };
         for (int s = 0; s < p.S; ++s) {
             const int cnt = fill(s, tid);
             signal_ready(s, tid);
@@ -674,20 +700,19 @@ struct Kern {
                     if (dead[s]) continue;
                     const int T = c.slab[s].T;
                     if (l < D) {
-                        for (int t = 0; t < T; ++t, ++gt) {
-                            if (!wait_tile(gt, tid)) return;
-                            store_tile(s, l, t, (uint32_t)((gt % R) * NCOL), tid);
-                        }
+                        for (int t = 0; t < T; ++t, ++gt)
+                            store_tile(s, l, t, (uint32_t)((gt % R) * NCOL), tid, wait_tile(gt, tid));
+                        if (!go_on()) return;
                         signal_ready(s, tid);
                     } else {
                         const int rows = TS * T;
-                        float *partF = reinterpret_cast<float *>(act_buf(s, (p.D - 1) & 1));
+                        // pooling partials go to the buffer layer D - 1 read (its MMAs are
+                        // done); the layer-D input buffer is still read by later tiles
+                        float *partF = reinterpret_cast<float *>(act_buf(s, p.D & 1));
                         int *partI = reinterpret_cast<int *>(partF + 4 * rows);
-                        for (int t = 0; t < T; ++t, ++gt) {
-                            if (!wait_tile(gt, tid)) return;
-                            pool_tile(s, t, (uint32_t)((gt % R) * NCOL), tid, partF, partI, rows);
-                        }
-                        epi_sync();
+                        for (int t = 0; t < T; ++t, ++gt)
+                            pool_tile(s, t, (uint32_t)((gt % R) * NCOL), tid, partF, partI, rows, wait_tile(gt, tid));
+                        if (!go_on()) return;
                         pool_finish(s, tid, partF, partI, rows);
                         const int cnt = fill(s, tid);
                         signal_ready(s, tid);
@@ -990,6 +1015,7 @@ extern "C" int vmc_debug_umma_selftest(const uint16_t *A_dev, const uint16_t *B_
 {
     if (!A_dev || !B_dev || !D_dev) return VMC_ERR_ARG;
     if (N < 16 || N > 128 || N % 16 || K < 16 || K > 32 || K % 16 || shift < 0 || shift > 64) return VMC_ERR_ARG;
+    if (variant && N > 64) return VMC_ERR_ARG;   // exchanged strides would read past the B buffer
     int dev = 0, maj = 0, mnr = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);

@@ -20,8 +20,9 @@ def test_umma_tile(N, K, shift):
     torch.cuda.synchronize()
     ref = A[shift:shift + 128].double() @ B.double().T
     err = (D.double() - ref).abs().max().item()
-    if err > 1e-3:
+    if err > 1e-3 and N <= 64:      # the exchanged-stride probe stays inside its buffer only for N <= 64
         D1 = umma_selftest(A, B, N, K, shift=shift, variant=1)
         torch.cuda.synchronize()
         err1 = (D1.double() - ref).abs().max().item()
         pytest.fail(f"UMMA layout mismatch: err={err} (variant with LBO/SBO exchanged: {err1})")
+    assert err <= 1e-3, err
