@@ -20,10 +20,10 @@
 // the padding columns are computed and dropped.  The embedding layer
 // (c_in = 1) uses a small im2col of the nine spins (K = 16, 7 zero).
 //
-// Warp roles: warps 0-15 (the "epilogue" group) build neighbours, drain
+// Warp roles: warps 0-7 (the "epilogue" group) build neighbours, drain
 // TMEM tile by tile (shift-add, bias, SiLU -> 16-bit into the next padded
 // buffer with the circular halo copies), pool the last layer and keep the
-// per-parent FP64 energy sums; warp 16 allocates TMEM and one lane issues
+// per-parent FP64 energy sums; warp 8 allocates TMEM and one lane issues
 // every MMA and the per-layer weight bulk copies (a two-deep ring).
 // Accumulators live in a ring of TMEM slots (one tile each) with full/empty
 // mbarriers, and two slabs alternate, so the epilogue of one tile overlaps
@@ -42,7 +42,7 @@
 namespace vmc {
 namespace tc {
 
-constexpr int NEPI_WARPS = 16;
+constexpr int NEPI_WARPS = 8;
 constexpr int NEPI = NEPI_WARPS * 32;     // epilogue threads
 constexpr int MMA_WARP = NEPI_WARPS;
 constexpr int NTHREADS = NEPI + 32;
@@ -107,10 +107,10 @@ struct Ctrl {
     double slot_la[2][MAX_SLOTS];
     int slot_sg[2][MAX_SLOTS];
     Parent ring[RING];
-    float xch[2][4][4][3 * 8];  // [tile parity][channel group][lane quarter][x1(lane0), x2(lane0), x2(lane1)]
+    float xch[2][2][4][3 * 16]; // [tile parity][channel group][lane quarter][x1(lane0), x2(lane0), x2(lane1)]
 };
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(2 + g) : "memory"); }
 
 // two FP32 values -> packed 16-bit pair (low half = a), round to nearest even
@@ -181,7 +181,7 @@ __device__ __forceinline__ void tmem_ld_n(uint32_t taddr, float (&v)[N])
 template <int C, bool F16>
 struct Kern {
     static constexpr uint32_t WB = 18 * C * C;    // bytes of one C -> C layer image
-    static constexpr int CPT = C / 4;             // channels per epilogue thread (4 channel groups)
+    static constexpr int CPT = C / 2;             // channels per epilogue thread (2 channel groups)
     static constexpr int NCOL = 3 * C;            // TMEM columns per tile slot
 
     const Params &p;
@@ -246,7 +246,9 @@ struct Kern {
         bool dead[2] = {false, p.S < 2};
         int cnt[2] = {0, 0};
         uint32_t ph_ar[2] = {0, 0};
-        long long step = 0, gt = 0;   // weight step, global tile counter
+        long long step = 0;           // weight step
+        int slot = 0;                 // TMEM slot of the next tile, and the parity of its use
+        uint32_t use_par = 0;
         bool ok = true;
         while (ok && !(dead[0] && dead[1])) {
             for (int l = 0; l <= D && ok; ++l) {
@@ -268,13 +270,12 @@ struct Kern {
                         any = true;
                     }
                     const int T = *(volatile int *)&c.slab[s].T;
-                    for (int t = 0; t < T; ++t, ++gt) {
-                        const int slot = (int)(gt % R);
-                        const uint32_t par = (uint32_t)(((gt / R) & 1) ^ 1);
-                        if (!wait_bar(&c.t_empty[slot], par, 3)) { ok = false; break; }
+                    for (int t = 0; t < T; ++t) {
+                        if (!wait_bar(&c.t_empty[slot], use_par ^ 1u, 3)) { ok = false; break; }
                         tc_fence_after();
                         issue_tile(s, l, t, (int)(step & 1), tmem + (uint32_t)(slot * NCOL));
                         umma_commit(&c.t_full[slot]);
+                        if (++slot == R) { slot = 0; use_par ^= 1u; }
                     }
                 }
                 if (!ok || !any) break;
@@ -311,113 +312,146 @@ struct Kern {
         x = X - j * (m.L + 2);
     }
 
+    // Per-(slab, layer) constants of the epilogue threads.
+    struct TileCtx {
+        int L, PW, count;
+        uint32_t mPW, mLP;
+        uint32_t out;           // output buffer (shared address)
+        float bias[CPT];
+    };
+
+    __device__ __forceinline__ void load_tctx(int s, int l, int tid, TileCtx &k) const
+    {
+        const SlabMeta &m = c.slab[s];
+        k.L = m.L; k.PW = m.PW; k.count = m.count; k.mPW = m.mPW; k.mLP = m.mLP;
+        k.out = smem_u32(act_buf(s, l & 1));
+        const int g = (tid >> 5) >> 2;
+        const float *bias = p.bias32 + l * C + g * CPT;
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) k.bias[i] = __ldg(bias + i);
+    }
+
     // Drain one tile: load the thread's CPT channels of P[q][kx C + co] for
-    // kx = 0 (and 1, 2 for C -> C layers), release the TMEM slot, and form
-    // z[q] = P0[q] + P1[q+1] + P2[q+2] across lanes.  Returns z (no bias).
-    __device__ void drain_tile(int l, int t, uint32_t slot_col, int tid, float (&z)[CPT], bool ok)
+    // kx = 0 (and 1, 2 for C -> C layers) under one wait, release the TMEM
+    // slot, and form z[q] = P0[q] + P1[q+1] + P2[q+2] + bias across lanes.
+    __device__ __forceinline__ void drain_tile(int l, int t, int slot, int tid, const TileCtx &k, float (&z)[CPT], bool ok)
     {
         const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
-        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + slot_col + (uint32_t)(g * CPT);
+        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(slot * NCOL + g * CPT);
         float x1[CPT], x2[CPT];
         if (!ok) {
 #pragma unroll
             for (int i = 0; i < CPT; ++i) { z[i] = 0.f; x1[i] = 0.f; x2[i] = 0.f; }
         } else if (l > 0) {
-            if constexpr (CPT == 8) tmem_ld8x3(taddr, C, z, x1, x2);
-            else tmem_ld4x3(taddr, C, z, x1, x2);
+            if constexpr (CPT == 16) tmem_ld16x3(taddr, C, z, x1, x2);
+            else tmem_ld8x3(taddr, C, z, x1, x2);
         } else {
             tmem_ld_n<CPT>(taddr, z);
         }
         tc_fence_before();
         __syncwarp();
-        if (ok && lane == 0) mbar_arrive(&c.t_empty[(slot_col / NCOL)]);
-        if (l == 0) return;
-        // rows q+1, q+2 of the next lane quarter, through shared memory
+        if (ok && lane == 0) mbar_arrive(&c.t_empty[slot]);
+        if (l == 0) {
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) z[i] += k.bias[i];
+            return;
+        }
+        // rows q+1, q+2 that live in the next lane quarter, through shared memory
         float *xo = c.xch[t & 1][g][wq];
-        if (wq > 0) {
+        if (wq > 0 && lane < 2) {
             if (lane == 0) {
 #pragma unroll
                 for (int i = 0; i < CPT; ++i) { xo[i] = x1[i]; xo[CPT + i] = x2[i]; }
-            } else if (lane == 1) {
+            } else {
 #pragma unroll
                 for (int i = 0; i < CPT; ++i) xo[2 * CPT + i] = x2[i];
             }
         }
         group_sync(g);
-        const float *xn = c.xch[t & 1][g][(wq + 1) & 3];
+        // lanes 30 and 31 take rows q+1 / q+2 from the next quarter; every lane
+        // then adds in the same order, so the arithmetic of a cell does not
+        // depend on where it sits in the tile
+        float a1[CPT], a2[CPT];
 #pragma unroll
         for (int i = 0; i < CPT; ++i) {
-            float a1 = __shfl_down_sync(0xffffffffu, x1[i], 1);
-            float a2 = __shfl_down_sync(0xffffffffu, x2[i], 2);
-            if (lane == 31) { a1 = xn[i]; a2 = xn[2 * CPT + i]; }
-            else if (lane == 30) { a2 = xn[CPT + i]; }
-            z[i] += a1 + a2;
+            a1[i] = __shfl_down_sync(0xffffffffu, x1[i], 1);
+            a2[i] = __shfl_down_sync(0xffffffffu, x2[i], 2);
         }
+        if (lane >= 30) {
+            const float *xn = c.xch[t & 1][g][(wq + 1) & 3];
+            const bool l31 = (lane == 31);
+#pragma unroll
+            for (int i = 0; i < CPT; ++i) {
+                if (l31) a1[i] = xn[i];
+                a2[i] = l31 ? xn[2 * CPT + i] : xn[CPT + i];
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) z[i] = ((z[i] + k.bias[i]) + a1[i]) + a2[i];
     }
 
-    // epilogue of one tile of a hidden layer: bias, SiLU, 16-bit, stores
-    __device__ void store_tile(int s, int l, int t, uint32_t slot_col, int tid, bool ok)
+    // epilogue of one tile of a hidden layer: SiLU, 16-bit, stores
+    __device__ __forceinline__ void store_tile(int l, int t, int slot, int tid, const TileCtx &k, bool ok)
     {
-        const SlabMeta &m = c.slab[s];
         const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
         float z[CPT];
-        drain_tile(l, t, slot_col, tid, z, ok);
+        drain_tile(l, t, slot, tid, k, z, ok);
         if (!ok) return;
         const int i_row = wq * 32 + lane;
         const int r = t * TS + i_row;
-        int y, j, x;
-        cell_coords(r, m, y, j, x);
-        const int L = m.L, PW = m.PW;
-        if (i_row < TS && y < L && x < L && j < m.count) {
-            const float *bias = p.bias32 + l * C + g * CPT;
+        const int y = (int)__umulhi((uint32_t)r, k.mPW);
+        const int X = r - y * k.PW;
+        const int j = (int)__umulhi((uint32_t)X, k.mLP);
+        const int x = X - j * (k.L + 2);
+        const int L = k.L;
+        if (i_row < TS && y < L && x < L && j < k.count) {
             uint32_t w[CPT / 2];
 #pragma unroll
-            for (int i = 0; i < CPT / 2; ++i)
-                w[i] = pack2<F16>(silu<F16>(z[2 * i] + __ldg(bias + 2 * i)), silu<F16>(z[2 * i + 1] + __ldg(bias + 2 * i + 1)));
-            const int R0 = (y + 1) * PW + j * (L + 2) + x + 1;
+            for (int i = 0; i < CPT / 2; ++i) w[i] = pack2<F16>(silu<F16>(z[2 * i]), silu<F16>(z[2 * i + 1]));
+            const int R0 = (y + 1) * k.PW + j * (L + 2) + x + 1;
             const int hx = (x == 0) ? L : ((x == L - 1) ? -L : 0);
-            const int vy = (y == 0) ? L * PW : ((y == L - 1) ? -L * PW : 0);
-            int rows[4];
-            int nr = 1;
-            rows[0] = R0;
-            if (hx) rows[nr++] = R0 + hx;
+            const int vy = (y == 0) ? L * k.PW : ((y == L - 1) ? -L * k.PW : 0);
+            // channel group g: C = 32 -> planes 2g, 2g + 1; C = 16 -> plane g
+            auto put = [&](int row) {
+                const uint32_t a = k.out + (uint32_t)row * 16u;
+                if constexpr (CPT == 16) {
+                    st_shared_v4(a + (2 * g) * PS, w[0], w[1], w[2], w[3]);
+                    st_shared_v4(a + (2 * g + 1) * PS, w[4], w[5], w[6], w[7]);
+                } else {
+                    st_shared_v4(a + g * PS, w[0], w[1], w[2], w[3]);
+                }
+            };
+            put(R0);
+            if (hx) put(R0 + hx);
             if (vy) {
-                rows[nr++] = R0 + vy;
-                if (hx) rows[nr++] = R0 + vy + hx;
-            }
-            const uint32_t out = smem_u32(act_buf(s, l & 1));
-            // channel group g: C = 32 -> plane g (8 channels, 16 B);
-            //                  C = 16 -> plane g/2, half (g & 1) (4 channels, 8 B)
-            for (int q = 0; q < nr; ++q) {
-                const uint32_t a = out + (uint32_t)rows[q] * 16u;
-                if constexpr (CPT == 8) st_shared_v4(a + g * PS, w[0], w[1], w[2], w[3]);
-                else st_shared_v2(a + (g >> 1) * PS + (g & 1) * 8u, w[0], w[1]);
+                put(R0 + vy);
+                if (hx) put(R0 + vy + hx);
             }
         }
     }
 
     // epilogue of one tile of the last layer: pooling partials
-    __device__ void pool_tile(int s, int t, uint32_t slot_col, int tid, float *partF, int *partI, int rows, bool ok)
+    __device__ __forceinline__ void pool_tile(int t, int slot, int tid, const TileCtx &k, float *partF, int *partI,
+                                              int rows, bool ok)
     {
-        const SlabMeta &m = c.slab[s];
         const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
         float z[CPT];
-        drain_tile(p.D, t, slot_col, tid, z, ok);
+        drain_tile(p.D, t, slot, tid, k, z, ok);
         if (!ok) return;
         const int i_row = wq * 32 + lane;
         const int r = t * TS + i_row;
-        int y, j, x;
-        cell_coords(r, m, y, j, x);
-        if (i_row < TS && y < m.L && x < m.L && j < m.count) {
-            const float *bias = p.bias32 + p.D * C + g * CPT;
+        const int y = (int)__umulhi((uint32_t)r, k.mPW);
+        const int X = r - y * k.PW;
+        const int j = (int)__umulhi((uint32_t)X, k.mLP);
+        const int x = X - j * (k.L + 2);
+        if (i_row < TS && y < k.L && x < k.L && j < k.count) {
             float sl = 0.f;
             int neg = 0, zer = 0;
 #pragma unroll
             for (int i = 0; i < CPT; ++i) {
-                const float v = z[i] + __ldg(bias + i);
-                sl += __log2f(fabsf(v));
-                neg += (v < 0.f);
-                zer += (v == 0.f);
+                sl += __log2f(fabsf(z[i]));
+                neg += (z[i] < 0.f);
+                zer += (z[i] == 0.f);
             }
             partF[g * rows + r] = sl;
             partI[g * rows + r] = neg | (zer << 16);
@@ -433,7 +467,7 @@ struct Kern {
         for (int j = warp; j < count; j += NEPI_WARPS) {
             double acc = 0.0;
             int neg = 0, zer = 0;
-            for (int idx = lane; idx < 4 * npix; idx += 32) {
+            for (int idx = lane; idx < 2 * npix; idx += 32) {
                 const int gg = idx / npix, pix = idx - gg * npix;
                 const int y = pix / L, x = pix - y * L;
                 const int r = y * m.PW + j * (L + 2) + x;
@@ -660,15 +694,15 @@ struct Kern {
         if (tid == 0) mbar_arrive(&c.act_ready[s]);
     }
 
-    // Each warp waits (one lane, bounded) for the accumulator slot of tile
-    // gt.  A warp whose wait fails keeps going through the tile loop without
-    // touching TMEM, so every named barrier still sees all participants; the
-    // whole epilogue returns together at the next CTA-wide check of c.abort.
-    __device__ bool wait_tile(long long gt, int tid)
+    // Each warp waits (one lane, bounded) for the accumulator slot of the
+    // next tile.  A warp whose wait fails keeps going through the tile loop
+    // without touching TMEM, so every named barrier still sees all
+    // participants; the whole epilogue returns together at the next CTA-wide
+    // check of c.abort.
+    __device__ __forceinline__ bool wait_tile(int slot, uint32_t par, int tid)
     {
-        const int R = p.nslots;
         int ok = 0;
-        if ((tid & 31) == 0) ok = wait_bar(&c.t_full[gt % R], (uint32_t)((gt / R) & 1), 7) ? 1 : 0;
+        if ((tid & 31) == 0) ok = wait_bar(&c.t_full[slot], par, 7) ? 1 : 0;
         ok = __shfl_sync(0xffffffffu, ok, 0);
         if (ok) tc_fence_after();
         return ok != 0;
@@ -678,17 +712,19 @@ struct Kern {
     {
         const int D = p.D, R = p.nslots;
         bool dead[2] = {false, true};
-        long long gt = 0;
+        int slot = 0;
+        uint32_t use_par = 0;
         int nchk = 0;
         // CTA-wide abort check: tid 0 snapshots c.abort into okf[parity]; the
         // next write to the same slot comes two barriers later, after every
         // thread has read this one
         auto go_on = [&]() {
-            const int k = (nchk++) & 1;
-            if (tid == 0) c.okf[k] = c.abort ? 0 : 1;
+            const int kk = (nchk++) & 1;
+            if (tid == 0) c.okf[kk] = c.abort ? 0 : 1;
             epi_sync();
-            return c.okf[k] != 0;
+            return c.okf[kk] != 0;
         };
+        auto next_slot = [&]() { if (++slot == R) { slot = 0; use_par ^= 1u; } };
         for (int s = 0; s < p.S; ++s) {
             const int cnt = fill(s, tid);
             signal_ready(s, tid);
@@ -699,9 +735,13 @@ struct Kern {
                 for (int s = 0; s < 2; ++s) {
                     if (dead[s]) continue;
                     const int T = c.slab[s].T;
+                    TileCtx k;
+                    load_tctx(s, l, tid, k);
                     if (l < D) {
-                        for (int t = 0; t < T; ++t, ++gt)
-                            store_tile(s, l, t, (uint32_t)((gt % R) * NCOL), tid, wait_tile(gt, tid));
+                        for (int t = 0; t < T; ++t) {
+                            store_tile(l, t, slot, tid, k, wait_tile(slot, use_par, tid));
+                            next_slot();
+                        }
                         if (!go_on()) return;
                         signal_ready(s, tid);
                     } else {
@@ -709,9 +749,11 @@ struct Kern {
                         // pooling partials go to the buffer layer D - 1 read (its MMAs are
                         // done); the layer-D input buffer is still read by later tiles
                         float *partF = reinterpret_cast<float *>(act_buf(s, p.D & 1));
-                        int *partI = reinterpret_cast<int *>(partF + 4 * rows);
-                        for (int t = 0; t < T; ++t, ++gt)
-                            pool_tile(s, t, (uint32_t)((gt % R) * NCOL), tid, partF, partI, rows, wait_tile(gt, tid));
+                        int *partI = reinterpret_cast<int *>(partF + 2 * rows);
+                        for (int t = 0; t < T; ++t) {
+                            pool_tile(t, slot, tid, k, partF, partI, rows, wait_tile(slot, use_par, tid));
+                            next_slot();
+                        }
                         if (!go_on()) return;
                         pool_finish(s, tid, partF, partI, rows);
                         const int cnt = fill(s, tid);
@@ -741,7 +783,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
         }
         for (int i = 0; i < MAX_TSLOTS; ++i) {
             mbar_init(&c.t_full[i], 1);
-            mbar_init(&c.t_empty[i], NEPI_WARPS);
+            mbar_init(&c.t_empty[i], NEPI_WARPS);   // one arrival per epilogue warp
         }
         mbar_init(&c.drain, 1);
         c.abort = 0;
