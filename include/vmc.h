@@ -74,6 +74,8 @@ typedef struct {
     int slab_configs;    /* configurations laid side by side in one slab */
     int slabs;           /* slabs in flight per CTA (1 or 2) */
     int ctas_per_sm;     /* persistent CTAs per SM */
+    int lane_cells;      /* lattice cells per accumulator row (TMEM lane), P:
+                            1..4 for C = 32, even 2..8 for C = 16 */
 } vmc_tiles;
 
 /* Create a context for L x L lattices with couplings J1, J2 (Eq. 3) and the

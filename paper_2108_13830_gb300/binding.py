@@ -35,7 +35,7 @@ class vmc_arch(ct.Structure):
 
 
 class vmc_tiles(ct.Structure):
-    _fields_ = [("slab_configs", ct.c_int), ("slabs", ct.c_int), ("ctas_per_sm", ct.c_int)]
+    _fields_ = [("slab_configs", ct.c_int), ("slabs", ct.c_int), ("ctas_per_sm", ct.c_int), ("lane_cells", ct.c_int)]
 
 
 _lib = None
@@ -233,14 +233,15 @@ class VMC:
     def debug_wait_timeout(self, budget_ns):
         self._check(lib().vmc_debug_wait_timeout(self._h, int(budget_ns), _stream()))
 
-    def set_tiles(self, L, slab_configs=0, slabs=0, ctas_per_sm=0):
-        t = vmc_tiles(slab_configs, slabs, ctas_per_sm)
+    def set_tiles(self, L, slab_configs=0, slabs=0, ctas_per_sm=0, lane_cells=0):
+        t = vmc_tiles(slab_configs, slabs, ctas_per_sm, lane_cells)
         self._check(lib().vmc_set_tiles(self._h, L, ct.byref(t)))
 
     def get_tiles(self, L):
         t = vmc_tiles()
         self._check(lib().vmc_get_tiles(self._h, L, ct.byref(t)))
-        return {"slab_configs": t.slab_configs, "slabs": t.slabs, "ctas_per_sm": t.ctas_per_sm}
+        return {"slab_configs": t.slab_configs, "slabs": t.slabs, "ctas_per_sm": t.ctas_per_sm,
+                "lane_cells": t.lane_cells}
 
     def autotune(self, L, probe_B=512):
         self._check(lib().vmc_autotune(self._h, L, int(probe_B), _stream()))

@@ -16,7 +16,7 @@ __global__ void umma_rate_kernel(int N, int count, unsigned long long *cycles, i
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tbase;
-    __shared__ int abort_flag;
+    __shared__ int abort_flag, wfl, wsite;   // the wait may raise status bits atomically
     const int tid = threadIdx.x, warp = tid >> 5;
     // A: 4 K-chunks of 128 rows (plane per 8 channels: 8 planes of 2 KB);
     // B: 4 K-chunks of N rows (32 N bytes each)
@@ -24,7 +24,7 @@ __global__ void umma_rate_kernel(int N, int count, unsigned long long *cycles, i
     uint8_t *Bs = sm + 16384;
     for (int i = tid; i < (16384 + 4 * 32 * N) / 16; i += blockDim.x)
         reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) { mbar_init(&bar, 1); mbar_fence_init(); abort_flag = 0; }
+    if (tid == 0) { mbar_init(&bar, 1); mbar_fence_init(); abort_flag = 0; wfl = 0; wsite = 0; }
     fence_proxy_async_smem();
     if (warp == 0) tmem_alloc(&tbase, 256);
     tc_fence_before();
@@ -40,8 +40,8 @@ __global__ void umma_rate_kernel(int N, int count, unsigned long long *cycles, i
                       i > 0);
         }
         umma_commit(&bar);
-        int fl = 0, site = 0;
-        mbar_wait_bounded(&bar, 0, &abort_flag, 2000000000LL, &fl, &site, 0);
+        mbar_wait_bounded(&bar, 0, &abort_flag, 2000000000LL, &wfl, &wsite, 0);
+        const int fl = wfl;
         const unsigned long long t1 = clock64();
         cycles[blockIdx.x] = t1 - t0;
         if (fl) atomicOr(status, fl);

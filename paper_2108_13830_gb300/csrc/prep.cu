@@ -76,15 +76,19 @@ __global__ void tc_image_kernel(const double *__restrict__ theta, uint16_t *img,
             if (k < 9) w = W[n * 9 + k];
         } else {
             const int ky = chunk / (C / 16), h = chunk % (C / 16);
-            const int kx = n / C, co = n % C;
+            // column block j of the B chunk holds horizontal tap kx = 2 - j
+            const int kx = 2 - n / C, co = n % C;
             const int ci = 16 * h + k;
             w = W[(co * C + ci) * 9 + ky * 3 + kx];
         }
+        // the tensor-core path computes h = z / 2 (SiLU(z) = h + h tanh h), so
+        // weights and biases are stored halved (exact: a power of two)
+        w *= 0.5;
         img[e] = f16 ? __half_as_ushort(__double2half(w)) : __bfloat16_as_ushort(__double2bfloat16(w));
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)(D + 1) * C; i += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(i / C), c = (int)(i % C);
-        bias32[i] = (float)theta[vmc_woffset(C, l) + 9LL * C * (l == 0 ? 1 : C) + c];
+        bias32[i] = (float)(0.5 * theta[vmc_woffset(C, l) + 9LL * C * (l == 0 ? 1 : C) + c]);
     }
 }
 

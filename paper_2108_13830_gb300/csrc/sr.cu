@@ -191,6 +191,54 @@ __global__ void rowdot_kernel(const float *__restrict__ O, int64_t m, int64_t n,
     if (lane == 0) t[row] = (double)acc.h + (double)acc.l;
 }
 
+// t_b = sum_k O_bk v_k for RB consecutive rows per CTA: each thread walks
+// column groups of 4, loads the split v once and applies it to the RB rows,
+// so v is read from L2 once per RB rows instead of once per row.
+template <int RB>
+__global__ void __launch_bounds__(256) rowdot_blk_kernel(const float *__restrict__ O, int64_t m, int64_t n,
+                                                         const float *__restrict__ vh, const float *__restrict__ vl,
+                                                         double *t)
+{
+    __shared__ float red_h[RB][8], red_l[RB][8];
+    const int64_t r0 = blockIdx.x * (int64_t)RB;
+    const int nr = (int)min((int64_t)RB, m - r0);
+    DF acc[RB];
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[r] = DF{0.f, 0.f};
+    const float4 *h4 = reinterpret_cast<const float4 *>(vh);
+    const float4 *l4 = reinterpret_cast<const float4 *>(vl);
+    const int64_t nq = n / 4;
+    for (int64_t q = threadIdx.x; q < nq; q += blockDim.x) {
+        const float4 h = __ldg(h4 + q), l = __ldg(l4 + q);
+#pragma unroll
+        for (int r = 0; r < RB; ++r) {
+            if (r < nr) {
+                const float4 a = __ldg(reinterpret_cast<const float4 *>(O + (r0 + r) * n) + q);
+                df_mac(acc[r], a.x, h.x, l.x);
+                df_mac(acc[r], a.y, h.y, l.y);
+                df_mac(acc[r], a.z, h.z, l.z);
+                df_mac(acc[r], a.w, h.w, l.w);
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+        DF a = acc[r];
+        for (int off = 16; off > 0; off >>= 1) {
+            const DF o = df_shfl_xor(a, off);
+            df_add_df(a, o);
+        }
+        if (lane == 0) { red_h[r][w] = a.h; red_l[r][w] = a.l; }
+    }
+    __syncthreads();
+    if (threadIdx.x < RB && (int)threadIdx.x < nr) {
+        DF a{0.f, 0.f};
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) df_add_df(a, DF{red_h[threadIdx.x][i], red_l[threadIdx.x][i]});
+        t[r0 + threadIdx.x] = (double)a.h + (double)a.l;
+    }
+}
+
 // ---------------------------------------------------------------- CG
 
 // q = u + shift p; partial dot p.q per CTA
@@ -349,7 +397,7 @@ static void launch_sv_partials(vmc_ctx *ctx, const float *O, int64_t m, const Sr
     const int64_t rpc = (m + nch - 1) / nch;
     const bool vec = vec_ok(O, n);
     const unsigned rows_grid = (unsigned)((m + 7) / 8);
-    if (vec) rowdot_kernel<true><<<rows_grid, 256, 0, s>>>(O, m, n, w.vh, w.vl, w.t);
+    if (vec) rowdot_blk_kernel<8><<<rows_grid, 256, 0, s>>>(O, m, n, w.vh, w.vl, w.t);
     else rowdot_kernel<false><<<rows_grid, 256, 0, s>>>(O, m, n, w.vh, w.vl, w.t);
     center_kernel<<<1, 1024, 0, s>>>(w.t, m, 1.0 / (double)m, w.scal + 1, w.wh, w.wl);
     const int V = vec ? 4 : 1;

@@ -6,30 +6,37 @@
 // bonds (Sec. 3.1, Fig. 2c) and streams sigma itself followed by every
 // exchange neighbour sigma' through the network.  Configurations are packed
 // into "slabs": G lattices side by side, each as (L+2) x (L+2) circularly
-// padded cells, so a slab is a PH x PW grid with PW = G (L+2), PH = L+2.
+// padded cells, so a slab is an (L+2) x PW grid of cells (PW >= G (L+2)).
 //
-// A C -> C layer is an implicit GEMM over tiles of 128 padded cells
-// (row-major, tile t starting at cell 126 t):
-//   P[q][kx C + co] = sum_{ky, ci} A[q + ky PW][ci] W[ky][kx][ci][co]
-// (the vertical tap is a start-address offset of the A descriptor, the
-// three horizontal taps are stacked along N = 3 C), so a tile takes 3 C/16
-// MMAs of 128 x 3C x 16.  The output of cell q is
-//   z[q][co] = P[q][co] + P[q+1][C + co] + P[q+2][2C + co],
-// which the epilogue forms across TMEM lanes with warp shuffles (the last
-// two rows of a tile are overlap rows, hence the stride 126).  Outputs at
-// the padding columns are computed and dropped.  The embedding layer
-// (c_in = 1) uses a small im2col of the nine spins (K = 16, 7 zero).
+// Lane packing.  A TMEM lane (an MMA row) holds P consecutive cells of a
+// grid row, so an accumulator tile is 128 lanes x P C columns and covers
+// 128 P cells; column i C + co of lane r is output channel co of cell
+// P r + i.  A C -> C layer (Eq. 5, 3 x 3 circular convolution) is an
+// implicit GEMM: for every vertical tap ky (an A start-address offset of
+// ky - 1 grid rows) and 16-channel K chunk h, input cell i of lane r feeds
+// outputs i - 1, i, i + 1 of the same lane through one MMA whose B operand
+// stacks the three horizontal taps along N (N = 3 C, fewer at the ends of
+// the lane) and whose D address starts at column (i - 1) C; the last cell of
+// lane r - 1 and the first of lane r + 1 feed outputs 0 and P - 1 through
+// two N = C MMAs on A shifted by one row.  No data crosses TMEM lanes, so
+// the epilogue is a plain per-lane bias + SiLU + store.  The MMAs of a
+// tile are issued in the order (previous lane, cells 0..P-1, next lane) for
+// every (ky, h): each output then sums its nine taps in the same order for
+// every P and every slab geometry, so results do not depend on the tiling.
+// Accumulators start from zero: the epilogue clears each TMEM slot as it
+// drains it.  The embedding layer (c_in = 1) uses an im2col of the nine
+// spins (K = 16, 7 zero), one N = C MMA per cell of the lane.
 //
-// Warp roles: warps 0-7 (the "epilogue" group) build neighbours, drain
-// TMEM tile by tile (shift-add, bias, SiLU -> 16-bit into the next padded
-// buffer with the circular halo copies), pool the last layer and keep the
-// per-parent FP64 energy sums; warp 8 allocates TMEM and one lane issues
-// every MMA and the per-layer weight bulk copies (a two-deep ring).
-// Accumulators live in a ring of TMEM slots (one tile each) with full/empty
-// mbarriers, and two slabs alternate, so the epilogue of one tile overlaps
-// the MMAs of the next.  Every mbarrier wait is bounded by a time budget; on
-// expiry the CTA raises VMC_ERR_TIMEOUT, drains its own copies and MMAs,
-// frees TMEM and returns.
+// Warp roles: warps 0-15 (the "epilogue" group) build neighbours, drain
+// TMEM tile by tile (bias, SiLU -> 16-bit into the next padded buffer with
+// the circular halo copies), pool the last layer and keep the per-parent
+// FP64 energy sums; warp 16 allocates TMEM and one lane issues every MMA and
+// the per-layer weight bulk copies (a two-deep ring).  Accumulators live in
+// a ring of TMEM slots (one tile each) with full/empty mbarriers, and two
+// slabs alternate, so the epilogue of one tile overlaps the MMAs of the
+// next.  Every mbarrier wait is bounded by a time budget; on expiry the CTA
+// raises VMC_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM and
+// returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <algorithm>
@@ -42,17 +49,20 @@
 namespace vmc {
 namespace tc {
 
-constexpr int NEPI_WARPS = 8;
+constexpr int NEPI_WARPS = 16;
 constexpr int NEPI = NEPI_WARPS * 32;     // epilogue threads
 constexpr int MMA_WARP = NEPI_WARPS;
 constexpr int NTHREADS = NEPI + 32;
 constexpr int MAX_SLOTS = 16;             // configurations per slab
+constexpr int MAX_P = 8;                  // cells per TMEM lane (P C <= 128 accumulator columns)
+constexpr int POOL_PARTS = 8;             // row blocks of a lattice summed separately by the pooling
 constexpr int RING = 32;                  // parents in flight per CTA
-constexpr int TS = 126;                   // tile stride in cells (128-row tiles overlap by 2)
 constexpr int MAX_TSLOTS = 16;            // TMEM accumulator slots
 constexpr int SMEM_LIMIT = 232448;
 
-struct Geo { int G, T, PW; };
+// slab geometry for one lattice side: configurations, cells per lane,
+// tiles per layer, grid row width in cells (a multiple of P)
+struct Geo { int G, P, T, PW; };
 
 struct Params {
     int mode;                   // 0 logpsi, 1 local energy
@@ -65,8 +75,9 @@ struct Params {
     double J1, J2;
     const uint8_t *wimg;
     const float *bias32;
-    int S, Rcap;
-    int nslots;                 // TMEM slots of 3 C columns
+    int S;
+    uint32_t BUF;               // bytes of one activation buffer
+    int slotc, nslots;          // TMEM columns per accumulator slot, slots
     Geo geo[17];
     double *out_a;
     int8_t *out_sign;
@@ -83,8 +94,9 @@ struct Parent {
 };
 
 struct SlabMeta {
-    int count, L, G, T, PW;
-    uint32_t mPW, mLP;          // floor(2^32 / PW) + 1, floor(2^32 / (L+2)) + 1: r / PW = umulhi(r, mPW)
+    int count, L, G, P, T, PW, RW, NRm;   // NRm = max(L RW - 128, 0): start of the last tile past the first
+    uint32_t PS;                          // plane stride (bytes)
+    uint32_t mRW, mLP;                    // magic(d) for d = RW, L + 2 (see udiv)
     int parent[MAX_SLOTS];
     int bond[MAX_SLOTS];
 };
@@ -104,14 +116,18 @@ struct Ctrl {
     int seg_first, seg_n;
     int nb_cnt, nb_a1, nb_a2, nb_par;
     SlabMeta slab[2];
-    double slot_la[2][MAX_SLOTS];
-    int slot_sg[2][MAX_SLOTS];
+    double pool_acc[MAX_SLOTS][POOL_PARTS];   // per-configuration pooling partials
+    int pool_nz[MAX_SLOTS][POOL_PARTS];
     Parent ring[RING];
-    float xch[2][2][4][3 * 16]; // [tile parity][channel group][lane quarter][x1(lane0), x2(lane0), x2(lane1)]
 };
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(2 + g) : "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+
+// x / d for 0 <= x < 2^16, 1 <= d < 2^10: umulhi(x, floor(2^32 / d) + 1) is
+// exact there for d >= 2; that multiplier does not fit 32 bits for d = 1,
+// which is encoded as 0
+__host__ __device__ __forceinline__ uint32_t udiv_magic(uint32_t d) { return d == 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
+__device__ __forceinline__ int udiv(int x, uint32_t m) { return m ? (int)__umulhi((uint32_t)x, m) : x; }
 
 // two FP32 values -> packed 16-bit pair (low half = a), round to nearest even
 template <bool F16>
@@ -126,16 +142,18 @@ __device__ __forceinline__ uint32_t pack2(float a, float b)
     }
 }
 
-// SiLU(z) = z / (1 + e^-z).  BF16 operands: z/2 (1 + tanh(z/2)) with the
-// hardware tanh (one MUFU op; its ~2^-11 error is below BF16 rounding for
-// the bulk of activations).  FP16 operands: e = exp(-|z|) (one MUFU op),
+// SiLU of z = 2 h, from h (the tensor-core weights and biases are halved).
+// BF16 operands: h (1 + tanh h) with the hardware tanh (one MUFU op; its
+// ~2^-11 error is below BF16 rounding for the bulk of activations).  FP16
+// operands: z / (1 + e^-z) with e = exp(-|z|) (one MUFU op) and
 // r = 1 / (1 + e) by Newton-Raphson from the linear estimate
 // 24/17 - 8/17 d on [1, 2] (relative error 1/17 -> (1/17)^4 after two
-// steps), sigmoid = r for z >= 0 and e r otherwise.
+// steps); sigmoid = r for z >= 0 and e r otherwise.
 template <bool F16>
-__device__ __forceinline__ float silu(float z)
+__device__ __forceinline__ float silu_h(float h)
 {
     if constexpr (F16) {
+        const float z = h + h;
         const float e = __expf(-fabsf(z));
         const float d = 1.0f + e;
         float r = fmaf(-0.47058823529f, d, 1.41176470588f);
@@ -143,7 +161,6 @@ __device__ __forceinline__ float silu(float z)
         r = r * fmaf(-d, r, 2.0f);
         return z * (z >= 0.f ? r : e * r);
     } else {
-        const float h = 0.5f * z;
         return fmaf(h, tanh_approx(h), h);
     }
 }
@@ -152,80 +169,202 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 {
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
-__device__ __forceinline__ void st_shared_v2(uint32_t addr, uint32_t a, uint32_t b)
-{
-    asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
-}
 
 __device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
 
-template <int N>
-__device__ __forceinline__ void tmem_ld_n(uint32_t taddr, float (&v)[N])
+// up to four 8-column TMEM loads (columns c, c + S, c + 2 S, c + 3 S of the
+// thread's lane) under one wait
+template <int N, uint32_t S>
+__device__ __forceinline__ void tmem_ld8_run(uint32_t ta, uint32_t (&r)[N][8])
 {
-    if constexpr (N == 8) tmem_ld8(taddr, v);
-    else if constexpr (N == 16) tmem_ld16(taddr, v);
-    else {
-        static_assert(N == 4, "4, 8 or 16 columns");
-        uint32_t r[4];
+    static_assert(N >= 1 && N <= 4, "1 to 4 chunks");
+    if constexpr (N == 1) {
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n\t"
             "tcgen05.wait::ld.sync.aligned;"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-            : "r"(taddr)
+            : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+              "=r"(r[0][7])
+            : "r"(ta)
             : "memory");
-#pragma unroll
-        for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+    } else if constexpr (N == 2) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+              "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]),
+              "=r"(r[1][6]), "=r"(r[1][7])
+            : "r"(ta), "r"(ta + S)
+            : "memory");
+    } else if constexpr (N == 3) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+              "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]),
+              "=r"(r[1][6]), "=r"(r[1][7]), "=r"(r[2][0]), "=r"(r[2][1]), "=r"(r[2][2]), "=r"(r[2][3]), "=r"(r[2][4]),
+              "=r"(r[2][5]), "=r"(r[2][6]), "=r"(r[2][7])
+            : "r"(ta), "r"(ta + S), "r"(ta + 2 * S)
+            : "memory");
+    } else {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+              "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]),
+              "=r"(r[1][6]), "=r"(r[1][7]), "=r"(r[2][0]), "=r"(r[2][1]), "=r"(r[2][2]), "=r"(r[2][3]), "=r"(r[2][4]),
+              "=r"(r[2][5]), "=r"(r[2][6]), "=r"(r[2][7]), "=r"(r[3][0]), "=r"(r[3][1]), "=r"(r[3][2]), "=r"(r[3][3]),
+              "=r"(r[3][4]), "=r"(r[3][5]), "=r"(r[3][6]), "=r"(r[3][7])
+            : "r"(ta), "r"(ta + S), "r"(ta + 2 * S), "r"(ta + 3 * S)
+            : "memory");
     }
 }
 
-template <int C, bool F16>
+// NM <= 8 chunks of 8 columns, S columns apart, under at most two waits
+template <int NM, uint32_t S>
+__device__ __forceinline__ void tmem_ld_chunks(uint32_t ta, float (&v)[NM][8])
+{
+    if constexpr (NM <= 4) {
+        uint32_t r[NM][8];
+        tmem_ld8_run<NM, S>(ta, r);
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[m][q] = __uint_as_float(r[m][q]);
+    } else {
+        uint32_t r[4][8], r2[NM - 4][8];
+        tmem_ld8_run<4, S>(ta, r);
+        tmem_ld8_run<NM - 4, S>(ta + 4 * S, r2);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+#pragma unroll
+            for (int m = 0; m < 4; ++m) v[m][q] = __uint_as_float(r[m][q]);
+#pragma unroll
+            for (int m = 4; m < NM; ++m) v[m][q] = __uint_as_float(r2[m - 4][q]);
+        }
+    }
+}
+
+// clear NM chunks of 8 columns, S columns apart (no wait)
+template <int NM, uint32_t S>
+__device__ __forceinline__ void tmem_zero_chunks_async(uint32_t ta)
+{
+    const uint32_t z = 0u;
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(ta + S * m),
+                     "r"(z)
+                     : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// clear NM chunks of 8 columns, S columns apart, and wait for the stores
+template <int NM, uint32_t S>
+__device__ __forceinline__ void tmem_zero_chunks(uint32_t ta)
+{
+    const uint32_t z = 0u;
+#pragma unroll
+    for (int m = 0; m < NM; ++m)
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(ta + S * m),
+                     "r"(z)
+                     : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// NM: 8-column accumulator chunks each epilogue thread drains per tile
+// (P C / 32), a compile-time constant so that the epilogue's registers are
+// allocated for exactly one shape
+template <int C, bool F16, int NM>
 struct Kern {
     static constexpr uint32_t WB = 18 * C * C;    // bytes of one C -> C layer image
-    static constexpr int CPT = C / 2;             // channels per epilogue thread (2 channel groups)
-    static constexpr int NCOL = 3 * C;            // TMEM columns per tile slot
+    static constexpr int CP8 = C / 8;             // 16-byte channel planes per cell
+    static constexpr int NCOL = 3 * C;            // rows of a C -> C B chunk
+    static constexpr int P = NM * 32 / C;         // cells per TMEM lane
 
     const Params &p;
     uint8_t *smem;
     Ctrl &c;
     int8_t *spins;
     uint16_t *list;
-    uint32_t BUF, PS;
     uint32_t tmem;
 
-    __device__ Kern(const Params &p_, uint8_t *smem_, Ctrl &c_, int8_t *sp, uint16_t *li, uint32_t buf, uint32_t tm)
-        : p(p_), smem(smem_), c(c_), spins(sp), list(li), BUF(buf), PS(p_.Rcap * 16u), tmem(tm) {}
+    __device__ Kern(const Params &p_, uint8_t *smem_, Ctrl &c_, int8_t *sp, uint16_t *li, uint32_t tm)
+        : p(p_), smem(smem_), c(c_), spins(sp), list(li), tmem(tm) {}
 
-    __device__ uint8_t *act_buf(int s, int k) const { return smem + 2 * WB + (size_t)(2 * s + k) * BUF; }
+    __device__ uint8_t *act_buf(int s, int k) const { return smem + 2 * WB + (size_t)(2 * s + k) * p.BUF; }
 
     __device__ bool wait_bar(uint64_t *bar, uint32_t parity, int site)
     {
         return mbar_wait_bounded(bar, parity, &c.abort, p.budget_ns, &p.status->flags, &p.status->timeout_site, site);
     }
 
-    // A0 (embedding im2col) rows per plane for a slab of T tiles
-    __device__ static int a0_rows(int T) { return TS * (T - 1) + 128; }
+    // Slab geometry for lattice side L.
+    __device__ void set_geometry(SlabMeta &m, int L, const Geo &g) const
+    {
+        m.L = L;
+        m.G = g.G;
+        m.P = g.P;
+        m.T = g.T;
+        m.PW = g.PW;
+        m.RW = g.PW / g.P;
+        m.NRm = max(L * m.RW - 128, 0);
+        m.PS = (p.BUF / (uint32_t)(g.P * CP8 * 16)) * 16u;
+        m.mRW = udiv_magic((uint32_t)m.RW);
+        m.mLP = udiv_magic((uint32_t)(L + 2));
+    }
+
+    // first A row (lane 0) of tile t
+    __device__ __forceinline__ static int tile_row(const SlabMeta &m, int t) { return m.RW + min(128 * t, m.NRm); }
 
     // ---------------------------------------------------------------- MMA
-    __device__ void issue_tile(int s, int l, int t, int bsel, uint32_t dcol)
+    // MMAs of one (ky, h) step, in the order: last cell of the previous lane
+    // (tap kx = 0 of output 0), cells 0..P-1 (cell i feeds output
+    // i + 1 - kx for the taps kx it reaches inside the lane), first cell of
+    // the next lane (tap kx = 2 of output P - 1); every output thus receives
+    // kx = 0, 1, 2 in this order.  ad / bd are the step's descriptors; the
+    // entries move only their start-address fields (16-byte units), which
+    // stay inside [0, 2^14).
+    __device__ __forceinline__ void issue_step(uint32_t dslot, uint64_t ad, uint64_t bd, uint32_t ps16) const
+    {
+        umma_bf16(dslot, ad + (uint64_t)((P - 1) * CP8) * ps16 - 1u, bd + 2 * C, idesc_f16kind(128, C, F16), 1);
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const int jlo = i == 0 ? 1 : 0, jhi = (P - i) < 2 ? (P - i) : 2;
+            umma_bf16(dslot + (uint32_t)((i - 1 + jlo) * C), ad + (uint64_t)(i * CP8) * ps16, bd + (uint64_t)(jlo * C),
+                      idesc_f16kind(128, (jhi - jlo + 1) * C, F16), 1);
+        }
+        umma_bf16(dslot + (uint32_t)((P - 1) * C), ad + 1u, bd, idesc_f16kind(128, C, F16), 1);
+    }
+
+    __device__ void issue_tile(int s, int l, int t, int bsel, uint32_t dslot)
     {
         const SlabMeta &m = c.slab[s];
         const uint32_t wb = smem_u32(smem + bsel * WB);
+        const uint32_t PS = m.PS, RW = (uint32_t)m.RW;
+        const int r0 = tile_row(m, t);
         if (l == 0) {
-            const uint32_t a0 = smem_u32(act_buf(s, 1));
-            const uint64_t ad = smem_desc(a0 + (uint32_t)(t * TS) * 16u, (uint32_t)a0_rows(m.T) * 16u, 128);
-            umma_bf16(dcol, ad, smem_desc(wb, 16 * C, 128), idesc_f16kind(128, C, F16), 0);
+            const uint32_t a0 = smem_u32(act_buf(s, 1)) + (uint32_t)(r0 + 1) * 16u;
+            const uint64_t bd = smem_desc(wb, 16 * C, 128), ad = smem_desc(a0, PS, 128);
+            const uint32_t ps16 = PS >> 4;
+#pragma unroll
+            for (int i = 0; i < P; ++i)
+                umma_bf16(dslot + (uint32_t)(i * C), ad + (uint64_t)(2 * i) * ps16, bd, idesc_f16kind(128, C, F16), 1);
         } else {
-            const uint64_t ad0 = smem_desc(smem_u32(act_buf(s, (l - 1) & 1)), PS, 128);
-            const uint64_t bd0 = smem_desc(wb, 16 * NCOL, 128);
-            const uint32_t idesc = idesc_f16kind(128, NCOL, F16);
-            const uint32_t plane2 = (2u * PS) >> 4;
-            const uint32_t rt = (uint32_t)(t * TS);
+            const uint32_t abase = smem_u32(act_buf(s, (l - 1) & 1)) + (uint32_t)(r0 + 1) * 16u;
+            const uint32_t ps16 = PS >> 4;
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                for (int h = 0; h < C / 16; ++h)
-                    umma_bf16(dcol, ad0 + (uint64_t)(rt + (uint32_t)(ky * m.PW) + h * plane2),
-                              bd0 + (uint64_t)((ky * (C / 16) + h) * 2 * NCOL), idesc, (ky | h) != 0);
+                for (int h = 0; h < C / 16; ++h) {
+                    const uint32_t arow = abase + (uint32_t)(ky - 1) * RW * 16u + (uint32_t)h * 2u * PS;
+                    const uint32_t bch = wb + (uint32_t)((ky * (C / 16) + h) * 32 * NCOL);
+                    issue_step(dslot, smem_desc(arow, PS, 128), smem_desc(bch, 16 * NCOL, 128), ps16);
+                }
         }
     }
 
@@ -273,7 +412,7 @@ struct Kern {
                     for (int t = 0; t < T; ++t) {
                         if (!wait_bar(&c.t_empty[slot], use_par ^ 1u, 3)) { ok = false; break; }
                         tc_fence_after();
-                        issue_tile(s, l, t, (int)(step & 1), tmem + (uint32_t)(slot * NCOL));
+                        issue_tile(s, l, t, (int)(step & 1), tmem + (uint32_t)(slot * p.slotc));
                         umma_commit(&c.t_full[slot]);
                         if (++slot == R) { slot = 0; use_par ^= 1u; }
                     }
@@ -301,180 +440,141 @@ struct Kern {
         mbar_wait_bounded(&c.drain, 0, &dummy_abort, cb, &p.status->flags, &p.status->timeout_site, 6);
     }
 
-    // ---------------------------------------------------------------- epilogue helpers
-    // (y, j, x) of padded cell r; j = configuration slot, x column in it
-    // (exact for r < 2^16 and divisors < 2^10: umulhi(r, floor(2^32/d) + 1) = floor(r/d))
-    __device__ __forceinline__ void cell_coords(int r, const SlabMeta &m, int &y, int &j, int &x) const
-    {
-        y = (int)__umulhi((uint32_t)r, m.mPW);
-        const int X = r - y * m.PW;
-        j = (int)__umulhi((uint32_t)X, m.mLP);
-        x = X - j * (m.L + 2);
-    }
-
-    // Per-(slab, layer) constants of the epilogue threads.
+    // ---------------------------------------------------------------- epilogue
+    // Per-(slab, layer) constants of the epilogue threads.  A thread of warp
+    // w drains TMEM lane quarter w & 3 and the 8-column chunks k = g4 + 4 m
+    // (g4 = w >> 2) of each tile: channel plane g = k % (C/8) of cell
+    // k / (C/8), i.e. plane g4 of cell m for C = 32, plane g4 & 1 of cell
+    // 2 m + g4 / 2 for C = 16; one bias vector per thread.
     struct TileCtx {
-        int L, PW, count;
-        uint32_t mPW, mLP;
+        int L, PW, RW, NRm, count, NQ;
+        uint32_t mRW, mLP, PS;
         uint32_t out;           // output buffer (shared address)
-        float bias[CPT];
+        float bias[8];
     };
 
     __device__ __forceinline__ void load_tctx(int s, int l, int tid, TileCtx &k) const
     {
         const SlabMeta &m = c.slab[s];
-        k.L = m.L; k.PW = m.PW; k.count = m.count; k.mPW = m.mPW; k.mLP = m.mLP;
+        k.L = m.L; k.PW = m.PW; k.RW = m.RW; k.NRm = m.NRm; k.count = m.count;
+        k.NQ = (m.L + 2) * m.PW;
+        k.mRW = m.mRW; k.mLP = m.mLP; k.PS = m.PS;
         k.out = smem_u32(act_buf(s, l & 1));
-        const int g = (tid >> 5) >> 2;
-        const float *bias = p.bias32 + l * C + g * CPT;
-#pragma unroll
-        for (int i = 0; i < CPT; ++i) k.bias[i] = __ldg(bias + i);
+        const int g = ((tid >> 5) >> 2) & (CP8 - 1);
+        const float4 *b4 = reinterpret_cast<const float4 *>(p.bias32 + l * C + g * 8);
+        const float4 lo = __ldg(b4), hi = __ldg(b4 + 1);
+        k.bias[0] = lo.x; k.bias[1] = lo.y; k.bias[2] = lo.z; k.bias[3] = lo.w;
+        k.bias[4] = hi.x; k.bias[5] = hi.y; k.bias[6] = hi.z; k.bias[7] = hi.w;
     }
 
-    // Drain one tile: load the thread's CPT channels of P[q][kx C + co] for
-    // kx = 0 (and 1, 2 for C -> C layers) under one wait, release the TMEM
-    // slot, and form z[q] = P0[q] + P1[q+1] + P2[q+2] + bias across lanes.
-    __device__ __forceinline__ void drain_tile(int l, int t, int slot, int tid, const TileCtx &k, float (&z)[CPT], bool ok)
+    // Chunks [M0, M0 + N) of a tile, values in v: for each chunk of an
+    // interior cell either store SiLU(z) (with its circular halo copies) or,
+    // for the last layer, the pooling partials.
+    template <int M0, int N, bool POOL>
+    __device__ __forceinline__ void put_chunks(const float (&v)[N][8], int g4, int r, int Y, int rX, int Yh,
+                                               const TileCtx &k, float *partF, int *partI)
     {
-        const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
-        const uint32_t taddr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(slot * NCOL + g * CPT);
-        float x1[CPT], x2[CPT];
-        if (!ok) {
+        const int L = k.L;
 #pragma unroll
-            for (int i = 0; i < CPT; ++i) { z[i] = 0.f; x1[i] = 0.f; x2[i] = 0.f; }
-        } else if (l > 0) {
-            if constexpr (CPT == 16) tmem_ld16x3(taddr, C, z, x1, x2);
-            else tmem_ld8x3(taddr, C, z, x1, x2);
-        } else {
-            tmem_ld_n<CPT>(taddr, z);
+        for (int mm = 0; mm < N; ++mm) {
+            const int m = M0 + mm;
+            // chunk k = g4 + 4 m: cell i, channel plane g
+            const int i = (CP8 == 4) ? m : 2 * m + (g4 >> 1);
+            const int g = g4 & (CP8 - 1);
+            const int X = P * rX + i;
+            const int j = udiv(X, k.mLP);
+            const int x = X - j * (L + 2) - 1;
+            if (x < 0 || x >= L || j >= k.count) continue;
+            float h[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) h[q] = v[mm][q] + k.bias[q];
+            if constexpr (POOL) {
+                float sl = 0.f;
+                int neg = 0, zer = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    sl += __log2f(fabsf(h[q]));
+                    neg += (h[q] < 0.f);
+                    zer += (h[q] == 0.f);
+                }
+                const int qc = Y * k.PW + X;
+                partF[g * k.NQ + qc] = sl + 8.0f;   // log2|z| = log2|h| + 1 per channel
+                partI[g * k.NQ + qc] = neg | (zer << 16);
+            } else {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = pack2<F16>(silu_h<F16>(h[2 * q]), silu_h<F16>(h[2 * q + 1]));
+                const uint32_t plane = k.out + (uint32_t)(i * CP8 + g) * k.PS;
+                st_shared_v4(plane + (uint32_t)(r + 1) * 16u, w[0], w[1], w[2], w[3]);
+                // circular halo copies: column X -/+ L, row L + 1 / 0, and the corner
+                const int hx = (x == 0) ? L : ((x == L - 1) ? -L : 0);
+                uint32_t hplane = 0;
+                int hr = 0;
+                if (hx) {
+                    const int X2 = X + hx;
+                    const int xr = X2 / P;
+                    hplane = k.out + (uint32_t)((X2 - xr * P) * CP8 + g) * k.PS;
+                    hr = xr;
+                    st_shared_v4(hplane + (uint32_t)(Y * k.RW + hr + 1) * 16u, w[0], w[1], w[2], w[3]);
+                }
+                if (Yh >= 0) {
+                    st_shared_v4(plane + (uint32_t)(Yh * k.RW + rX + 1) * 16u, w[0], w[1], w[2], w[3]);
+                    if (hx) st_shared_v4(hplane + (uint32_t)(Yh * k.RW + hr + 1) * 16u, w[0], w[1], w[2], w[3]);
+                }
+            }
+        }
+    }
+
+    // One tile: load the thread's NM chunks under one wait, start clearing
+    // them, put the values, and release the slot once the clearing stores
+    // have completed.
+    template <bool POOL>
+    __device__ __forceinline__ void epi_tile(int t, int slot, int tid, const TileCtx &k, bool ok, float *partF,
+                                             int *partI)
+    {
+        const int warp = tid >> 5, lane = tid & 31, wq = warp & 3, g4 = warp >> 2;
+        const uint32_t ta = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(slot * p.slotc + 8 * g4);
+        const int r = k.RW + min(128 * t, k.NRm) + wq * 32 + lane;
+        const int Y = udiv(r, k.mRW);
+        const int rX = r - Y * k.RW;
+        const int L = k.L;
+        const int Yh = (Y == 1) ? L + 1 : ((Y == L) ? 0 : -1);
+        float v[NM][8];
+        if (ok) {
+            tmem_ld_chunks<NM, 32>(ta, v);
+            tmem_zero_chunks_async<NM, 32>(ta);
+            if (Y >= 1 && Y <= L) put_chunks<0, NM, POOL>(v, g4, r, Y, rX, Yh, k, partF, partI);
+            __syncwarp();
+            tmem_wait_st();
         }
         tc_fence_before();
         __syncwarp();
         if (ok && lane == 0) mbar_arrive(&c.t_empty[slot]);
-        if (l == 0) {
-#pragma unroll
-            for (int i = 0; i < CPT; ++i) z[i] += k.bias[i];
-            return;
-        }
-        // rows q+1, q+2 that live in the next lane quarter, through shared memory
-        float *xo = c.xch[t & 1][g][wq];
-        if (wq > 0 && lane < 2) {
-            if (lane == 0) {
-#pragma unroll
-                for (int i = 0; i < CPT; ++i) { xo[i] = x1[i]; xo[CPT + i] = x2[i]; }
-            } else {
-#pragma unroll
-                for (int i = 0; i < CPT; ++i) xo[2 * CPT + i] = x2[i];
-            }
-        }
-        group_sync(g);
-        // lanes 30 and 31 take rows q+1 / q+2 from the next quarter; every lane
-        // then adds in the same order, so the arithmetic of a cell does not
-        // depend on where it sits in the tile
-        float a1[CPT], a2[CPT];
-#pragma unroll
-        for (int i = 0; i < CPT; ++i) {
-            a1[i] = __shfl_down_sync(0xffffffffu, x1[i], 1);
-            a2[i] = __shfl_down_sync(0xffffffffu, x2[i], 2);
-        }
-        if (lane >= 30) {
-            const float *xn = c.xch[t & 1][g][(wq + 1) & 3];
-            const bool l31 = (lane == 31);
-#pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                if (l31) a1[i] = xn[i];
-                a2[i] = l31 ? xn[2 * CPT + i] : xn[CPT + i];
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < CPT; ++i) z[i] = ((z[i] + k.bias[i]) + a1[i]) + a2[i];
     }
 
-    // epilogue of one tile of a hidden layer: SiLU, 16-bit, stores
-    __device__ __forceinline__ void store_tile(int l, int t, int slot, int tid, const TileCtx &k, bool ok)
-    {
-        const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
-        float z[CPT];
-        drain_tile(l, t, slot, tid, k, z, ok);
-        if (!ok) return;
-        const int i_row = wq * 32 + lane;
-        const int r = t * TS + i_row;
-        const int y = (int)__umulhi((uint32_t)r, k.mPW);
-        const int X = r - y * k.PW;
-        const int j = (int)__umulhi((uint32_t)X, k.mLP);
-        const int x = X - j * (k.L + 2);
-        const int L = k.L;
-        if (i_row < TS && y < L && x < L && j < k.count) {
-            uint32_t w[CPT / 2];
-#pragma unroll
-            for (int i = 0; i < CPT / 2; ++i) w[i] = pack2<F16>(silu<F16>(z[2 * i]), silu<F16>(z[2 * i + 1]));
-            const int R0 = (y + 1) * k.PW + j * (L + 2) + x + 1;
-            const int hx = (x == 0) ? L : ((x == L - 1) ? -L : 0);
-            const int vy = (y == 0) ? L * k.PW : ((y == L - 1) ? -L * k.PW : 0);
-            // channel group g: C = 32 -> planes 2g, 2g + 1; C = 16 -> plane g
-            auto put = [&](int row) {
-                const uint32_t a = k.out + (uint32_t)row * 16u;
-                if constexpr (CPT == 16) {
-                    st_shared_v4(a + (2 * g) * PS, w[0], w[1], w[2], w[3]);
-                    st_shared_v4(a + (2 * g + 1) * PS, w[4], w[5], w[6], w[7]);
-                } else {
-                    st_shared_v4(a + g * PS, w[0], w[1], w[2], w[3]);
-                }
-            };
-            put(R0);
-            if (hx) put(R0 + hx);
-            if (vy) {
-                put(R0 + vy);
-                if (hx) put(R0 + vy + hx);
-            }
-        }
-    }
-
-    // epilogue of one tile of the last layer: pooling partials
-    __device__ __forceinline__ void pool_tile(int t, int slot, int tid, const TileCtx &k, float *partF, int *partI,
-                                              int rows, bool ok)
-    {
-        const int warp = tid >> 5, lane = tid & 31, g = warp >> 2, wq = warp & 3;
-        float z[CPT];
-        drain_tile(p.D, t, slot, tid, k, z, ok);
-        if (!ok) return;
-        const int i_row = wq * 32 + lane;
-        const int r = t * TS + i_row;
-        const int y = (int)__umulhi((uint32_t)r, k.mPW);
-        const int X = r - y * k.PW;
-        const int j = (int)__umulhi((uint32_t)X, k.mLP);
-        const int x = X - j * (k.L + 2);
-        if (i_row < TS && y < k.L && x < k.L && j < k.count) {
-            float sl = 0.f;
-            int neg = 0, zer = 0;
-#pragma unroll
-            for (int i = 0; i < CPT; ++i) {
-                sl += __log2f(fabsf(z[i]));
-                neg += (z[i] < 0.f);
-                zer += (z[i] == 0.f);
-            }
-            partF[g * rows + r] = sl;
-            partI[g * rows + r] = neg | (zer << 16);
-        }
-    }
-
-    // per-configuration FP64 sums and the per-parent bookkeeping
-    __device__ void pool_finish(int s, int tid, const float *partF, const int *partI, int rows)
+    // Per-configuration FP64 sums and the per-parent bookkeeping.  Each
+    // configuration's lattice is cut into POOL_PARTS blocks of rows; warps
+    // take (configuration, block) tasks, and thread 0 adds the blocks in
+    // order, so the summation order depends on L only, not on the slab.
+    __device__ void pool_finish(int s, int tid, const float *partF, const int *partI, int NQ)
     {
         SlabMeta &m = c.slab[s];
         const int warp = tid >> 5, lane = tid & 31;
-        const int L = m.L, count = m.count, npix = L * L;
-        for (int j = warp; j < count; j += NEPI_WARPS) {
+        const int L = m.L, count = m.count, PW = m.PW;
+        for (int task = warp; task < count * POOL_PARTS; task += NEPI_WARPS) {
+            const int j = task / POOL_PARTS, part = task - j * POOL_PARTS;
+            const int y0 = part * L / POOL_PARTS, y1 = (part + 1) * L / POOL_PARTS;
             double acc = 0.0;
             int neg = 0, zer = 0;
-            for (int idx = lane; idx < 2 * npix; idx += 32) {
-                const int gg = idx / npix, pix = idx - gg * npix;
-                const int y = pix / L, x = pix - y * L;
-                const int r = y * m.PW + j * (L + 2) + x;
-                acc += (double)partF[gg * rows + r];
-                const int nz = partI[gg * rows + r];
-                neg += nz & 0xffff;
-                zer += nz >> 16;
+            if (lane < L) {
+                for (int gg = 0; gg < CP8; ++gg)
+                    for (int y = y0; y < y1; ++y) {
+                        const int q = gg * NQ + (y + 1) * PW + j * (L + 2) + lane + 1;
+                        acc += (double)partF[q];
+                        const int nz = partI[q];
+                        neg += nz & 0xffff;
+                        zer += nz >> 16;
+                    }
             }
             for (int o = 16; o > 0; o >>= 1) {
                 acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -482,16 +582,23 @@ struct Kern {
                 zer += __shfl_xor_sync(0xffffffffu, zer, o);
             }
             if (lane == 0) {
-                c.slot_la[s][j] = zer ? -INFINITY : acc * 0.69314718055994530942;
-                c.slot_sg[s][j] = zer ? 0 : ((neg & 1) ? -1 : 1);
+                c.pool_acc[j][part] = acc;
+                c.pool_nz[j][part] = (neg & 0xffff) | (zer << 16);
             }
         }
         epi_sync();
         if (tid == 0) {
             for (int j = 0; j < count; ++j) {
+                double acc = 0.0;
+                int neg = 0, zer = 0;
+                for (int part = 0; part < POOL_PARTS; ++part) {
+                    acc += c.pool_acc[j][part];
+                    neg += c.pool_nz[j][part] & 0xffff;
+                    zer += c.pool_nz[j][part] >> 16;
+                }
+                const double la = zer ? -INFINITY : acc * 0.69314718055994530942;
+                const int sg = zer ? 0 : ((neg & 1) ? -1 : 1);
                 Parent &P = c.ring[m.parent[j]];
-                const double la = c.slot_la[s][j];
-                const int sg = c.slot_sg[s][j];
                 if (m.bond[j] < 0) {
                     P.la0 = la;
                     P.sg0 = sg;
@@ -532,14 +639,15 @@ struct Kern {
         }
     }
 
-    // Build the embedding-layer im2col rows of slots [first, first+n):
-    // nine spins of sigma' around each cell, 16 values per row in two planes.
+    // Build the embedding-layer im2col rows of slots [first, first+n): nine
+    // spins of sigma' around each interior cell, 16 values in two planes
+    // (planes 2 i, 2 i + 1 for cell i of its lane).
     __device__ void build_rows(int s, int first, int n, int tid)
     {
         const SlabMeta &m = c.slab[s];
         const int L = m.L, PW = m.PW, npix = L * L;
         const uint32_t a0 = smem_u32(act_buf(s, 1));
-        const uint32_t plane = (uint32_t)a0_rows(m.T) * 16u;
+        const uint32_t PS = m.PS;
         const uint32_t up = F16 ? 0x3C00u : 0x3F80u, dn = F16 ? 0xBC00u : 0xBF80u;
         for (int idx = tid; idx < n * npix; idx += NEPI) {
             const int jj = first + idx / npix, pix = idx - (idx / npix) * npix;
@@ -563,9 +671,12 @@ struct Kern {
                     h[ky * 3 + kx] = v > 0 ? up : dn;
                 }
             }
-            const uint32_t q = (uint32_t)(y * PW + jj * (L + 2) + x) * 16u;
-            st_shared_v4(a0 + q, h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
-            st_shared_v4(a0 + plane + q, h[8], 0u, 0u, 0u);
+            const int q = (y + 1) * PW + jj * (L + 2) + x + 1;
+            const int r = q / P;
+            const int i = q - r * P;
+            const uint32_t a = a0 + 2u * (uint32_t)i * PS + (uint32_t)(r + 1) * 16u;
+            st_shared_v4(a, h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+            st_shared_v4(a + PS, h[8], 0u, 0u, 0u);
         }
     }
 
@@ -641,18 +752,14 @@ struct Kern {
                 epi_sync();
             }
             if (tid == 0) {
-                if (m.count == 0) {
-                    // the slab takes the geometry of the lattice now at the cursor
-                    // (a new parent, or the rest of the previous fill's parent)
-                    const int Lc = c.cur_L;
-                    m.L = Lc;
-                    m.G = p.geo[Lc >> 1].G;
-                    m.T = p.geo[Lc >> 1].T;
-                    m.PW = p.geo[Lc >> 1].PW;
-                    m.mPW = (uint32_t)(0xFFFFFFFFu / (uint32_t)m.PW) + 1u;
-                    m.mLP = (uint32_t)(0xFFFFFFFFu / (uint32_t)(Lc + 2)) + 1u;
+                // the slab takes the geometry of the lattice now at the cursor
+                // (a new parent, or the rest of the previous fill's parent)
+                if (m.count == 0) set_geometry(m, c.cur_L, p.geo[c.cur_L >> 1]);
+                if (m.G < 1 || m.G > MAX_SLOTS || m.P != P) {
+                    c.abort = 1;
+                    atomicOr(&p.status->flags, VMC_STATUS_INTERNAL);
+                    m.G = 1;
                 }
-                if (m.G < 1 || m.G > MAX_SLOTS) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); m.G = 1; }
                 const int n_take = min(m.G - m.count, c.cur_nlist + 1 - c.cur_k);
                 for (int i = 0; i < n_take; ++i) {
                     const int kk = c.cur_k + i;
@@ -669,22 +776,9 @@ struct Kern {
             epi_sync();
             if (m.count >= m.G) break;
         }
-        const int count = m.count;
-        if (count > 0) {
-            // rows that belong to no configuration: zero (finite) input
-            const int L = m.L, rows = a0_rows(m.T);
-            const uint32_t a0 = smem_u32(act_buf(s, 1));
-            const uint32_t plane = (uint32_t)rows * 16u;
-            for (int r = tid; r < rows; r += NEPI) {
-                int y, j, x;
-                cell_coords(r, m, y, j, x);
-                if (!(y < L && x < L && j < count)) {
-                    st_shared_v4(a0 + r * 16u, 0u, 0u, 0u, 0u);
-                    st_shared_v4(a0 + plane + r * 16u, 0u, 0u, 0u, 0u);
-                }
-            }
-        }
-        return count;
+        // cells of no configuration keep whatever the buffer held: they feed
+        // only outputs that are dropped
+        return m.count;
     }
 
     __device__ void signal_ready(int s, int tid)
@@ -708,9 +802,20 @@ struct Kern {
         return ok != 0;
     }
 
+    // one (slab, layer) of tiles
+    template <bool POOL>
+    __device__ __forceinline__ void run_tiles(int T, int &slot, uint32_t &use_par, int tid, const TileCtx &k,
+                                              float *partF, int *partI)
+    {
+        for (int t = 0; t < T; ++t) {
+            epi_tile<POOL>(t, slot, tid, k, wait_tile(slot, use_par, tid), partF, partI);
+            if (++slot == p.nslots) { slot = 0; use_par ^= 1u; }
+        }
+    }
+
     __device__ void epilogue_role(int tid)
     {
-        const int D = p.D, R = p.nslots;
+        const int D = p.D;
         bool dead[2] = {false, true};
         int slot = 0;
         uint32_t use_par = 0;
@@ -724,7 +829,6 @@ struct Kern {
             epi_sync();
             return c.okf[kk] != 0;
         };
-        auto next_slot = [&]() { if (++slot == R) { slot = 0; use_par ^= 1u; } };
         for (int s = 0; s < p.S; ++s) {
             const int cnt = fill(s, tid);
             signal_ready(s, tid);
@@ -738,24 +842,17 @@ struct Kern {
                     TileCtx k;
                     load_tctx(s, l, tid, k);
                     if (l < D) {
-                        for (int t = 0; t < T; ++t) {
-                            store_tile(l, t, slot, tid, k, wait_tile(slot, use_par, tid));
-                            next_slot();
-                        }
+                        run_tiles<false>(T, slot, use_par, tid, k, nullptr, nullptr);
                         if (!go_on()) return;
                         signal_ready(s, tid);
                     } else {
-                        const int rows = TS * T;
                         // pooling partials go to the buffer layer D - 1 read (its MMAs are
                         // done); the layer-D input buffer is still read by later tiles
                         float *partF = reinterpret_cast<float *>(act_buf(s, p.D & 1));
-                        int *partI = reinterpret_cast<int *>(partF + 2 * rows);
-                        for (int t = 0; t < T; ++t) {
-                            pool_tile(t, slot, tid, k, partF, partI, rows, wait_tile(slot, use_par, tid));
-                            next_slot();
-                        }
+                        int *partI = reinterpret_cast<int *>(partF + CP8 * k.NQ);
+                        run_tiles<true>(T, slot, use_par, tid, k, partF, partI);
                         if (!go_on()) return;
-                        pool_finish(s, tid, partF, partI, rows);
+                        pool_finish(s, tid, partF, partI, k.NQ);
                         const int cnt = fill(s, tid);
                         signal_ready(s, tid);
                         dead[s] = (cnt == 0);
@@ -766,13 +863,12 @@ struct Kern {
     }
 };
 
-template <int C, bool F16>
+template <int C, bool F16, int NM>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_constant__ Params p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t BUF = (uint32_t)(C / 8) * p.Rcap * 16u;
-    Ctrl &c = *reinterpret_cast<Ctrl *>(smem + 2 * Kern<C, F16>::WB + (size_t)2 * p.S * BUF);
+    Ctrl &c = *reinterpret_cast<Ctrl *>(smem + 2 * Kern<C, F16, NM>::WB + (size_t)2 * p.S * p.BUF);
     int8_t *spins = reinterpret_cast<int8_t *>(&c + 1);
     uint16_t *list = reinterpret_cast<uint16_t *>(spins + ((p.L_max * p.L_max + 15) & ~15));
     if (tid == 0) {
@@ -788,7 +884,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
         mbar_init(&c.drain, 1);
         c.abort = 0;
         c.cur_parent = -1; c.cur_k = 0; c.cur_nlist = -1; c.cur_L = 0;
-        for (int i = 0; i < 2; ++i) { c.slab[i].count = 0; c.slab[i].L = 0; c.slab[i].G = 0; c.slab[i].T = 0; c.slab[i].PW = 0; }
+        for (int i = 0; i < 2; ++i) { c.slab[i].count = 0; c.slab[i].L = 0; c.slab[i].G = 0; c.slab[i].T = 0; }
         c.pending_b = -1; c.no_more = 0; c.ring_head = 0;
         for (int r = 0; r < RING; ++r) c.ring[r].valid = 0;
         mbar_fence_init();
@@ -798,7 +894,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    Kern<C, F16> k(p, smem, c, spins, list, BUF, c.tmem_base);
+    // accumulators start from zero: every MMA accumulates, and the epilogue
+    // clears each slot it drains
+    if (warp < MMA_WARP) {
+        const uint32_t ta = c.tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 128);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) tmem_zero_chunks<4, 32>(ta + 8u * q);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    Kern<C, F16, NM> k(p, smem, c, spins, list, c.tmem_base);
     if (warp < MMA_WARP) k.epilogue_role(tid);
     else if ((tid & 31) == 0) k.mma_role();
     tc_fence_before();
@@ -817,38 +923,93 @@ static size_t ctrl_bytes(int L_max)
     return sizeof(Ctrl) + ((L_max * L_max + 15) & ~15) + (size_t)4 * L_max * L_max * 2 + 64;
 }
 
-// tiles and shared-memory rows (per plane) of a slab of G lattices of side L
-static int rows_needed(int L, int G, int *T_out)
+// Slab of G lattices of side L with P cells per TMEM lane: tiles per layer,
+// grid row width, and the rows per plane any MMA or store of the slab
+// touches (row 0 is a spare row in front of the grid).
+static int geo_rows(int L, int G, int P, int *T_out, int *PW_out)
 {
-    const int PW = G * (L + 2);
-    const int T = (L * PW + TS - 1) / TS;
+    const int PW = (G * (L + 2) + P - 1) / P * P;
+    const int RW = PW / P;
+    const int NR = L * RW;
+    const int T = (NR + 127) / 128;
+    const int r_last = RW + std::min(128 * (T - 1), std::max(NR - 128, 0));
     *T_out = T;
-    const int mma_rows = TS * (T - 1) + 128 + 2 * PW;   // last A row any MMA of the slab reads, + 1
-    return (std::max((L + 2) * PW, mma_rows) + 7) & ~7;
+    *PW_out = PW;
+    return std::max((L + 2) * RW, r_last + 128 + RW + 1) + 1;
+}
+
+// issue cycles of one 128 x N x 16 MMA (measured on sm_103a: flat below
+// N = 64, then limited by the shared-memory operand reads)
+static double mma_cycles(int N) { return N <= 64 ? 50.0 : (N <= 96 ? 56.0 : 64.0 + (N - 128) * 0.5); }
+
+// modelled MMA cycles per tile of a C -> C layer
+static double tile_cycles(int C, int P)
+{
+    double per = 2 * mma_cycles(C);
+    for (int i = 0; i < P; ++i) {
+        const int jlo = std::max(0, 1 - i), jhi = std::min(2, P - i);
+        per += mma_cycles((jhi - jlo + 1) * C);
+    }
+    return per * 3 * (C / 16);
+}
+
+// P C <= 128 keeps at most 64 accumulator values per epilogue thread and
+// at least four TMEM slots
+static bool p_allowed(int C, int P)
+{
+    if (P < 1 || P > MAX_P || P * C > 128) return false;
+    return (P * C) % 32 == 0;
+}
+
+struct Cand {
+    Geo g;
+    double score;   // modelled cycles per useful lattice cell
+};
+
+// every geometry of lattice L within `buf` bytes per buffer, with its score
+static void geo_cands(int C, int L, uint32_t buf, int S, std::vector<Cand> &out)
+{
+    for (int P = 1; P <= MAX_P; ++P) {
+        if (!p_allowed(C, P)) continue;
+        for (int G = 1; G <= MAX_SLOTS; ++G) {
+            int T, PW;
+            const int rows = geo_rows(L, G, P, &T, &PW);
+            if ((size_t)rows * P * C * 2 > buf) break;
+            double sc = T * tile_cycles(C, P) / ((double)G * L * L);
+            if (S == 1) sc *= 1.0 + 0.5 / T;   // one slab: the layer barrier is not overlapped
+            out.push_back(Cand{Geo{G, P, T, PW}, sc});
+        }
+    }
 }
 
 struct Plan {
-    int S, Rcap;
+    int S, P;
+    uint32_t BUF;
+    int slotc;
     Geo geo[17];
     size_t smem;
 };
 
-// Largest-efficiency G for lattice L under the row capacity.
-static Geo best_geo(int L, int Rcap, int Gwant)
+static uint32_t buf_bytes(int C, int S, int L_max)
 {
-    Geo best{0, 0, 0};
-    double be = -1.0;
-    for (int G = 1; G <= MAX_SLOTS; ++G) {
-        int T;
-        const int R = rows_needed(L, G, &T);
-        if (R > Rcap) break;
-        const double eff = (double)L * L * G / (double)(TS * T);
-        if (Gwant > 0) {
-            if (G == Gwant) { best = Geo{G, T, G * (L + 2)}; be = eff; }
-            continue;
-        }
-        if (eff > be + 1e-9) { be = eff; best = Geo{G, T, G * (L + 2)}; }
+    const size_t wb = 2 * (size_t)(18 * C * C);
+    const size_t avail = SMEM_LIMIT - wb - ctrl_bytes(L_max) - 1024;
+    return (uint32_t)((avail / (2 * (size_t)S)) & ~(size_t)127);
+}
+
+// best geometry of lattice L under the tile choice `tc` (0 fields free)
+static Geo pick_geo(int C, int L, int S, uint32_t buf, const TileChoice &tc, double *score)
+{
+    std::vector<Cand> cs;
+    geo_cands(C, L, buf, S, cs);
+    Geo best{0, 0, 0, 0};
+    double bs = 1e300;
+    for (const Cand &cd : cs) {
+        if (tc.slab_configs && cd.g.G != tc.slab_configs) continue;
+        if (tc.lane_cells && cd.g.P != tc.lane_cells) continue;
+        if (cd.score < bs - 1e-12) { bs = cd.score; best = cd.g; }
     }
+    if (score) *score = bs;
     return best;
 }
 
@@ -858,40 +1019,44 @@ static int make_plan(const vmc_ctx *ctx, int L_main, int L_max, bool ragged, Pla
     TileChoice tc;
     auto it = ctx->tiles.find(L_main);
     if (it != ctx->tiles.end()) tc = it->second;
-    const int S = tc.slabs ? tc.slabs : 2;
-    const size_t wb = 2 * (size_t)(18 * C * C);
-    const size_t ctrl = ctrl_bytes(L_max);
-    const size_t avail = SMEM_LIMIT - wb - ctrl - 1024;
-    int Rcap = (int)(avail / ((size_t)2 * S * (C / 8) * 16)) & ~7;
-    Geo gmain = best_geo(L_main, Rcap, tc.slab_configs);
-    if (gmain.G == 0) return VMC_ERR_UNSUPPORTED;
-    if (!ragged) {
-        int T;
-        Rcap = rows_needed(L_main, gmain.G, &T);
+    int S = tc.slabs;
+    if (!S) {
+        // the slab count with the better modelled geometry for L_main
+        double s1 = 0, s2 = 0;
+        const Geo g1 = pick_geo(C, L_main, 1, buf_bytes(C, 1, L_max), tc, &s1);
+        const Geo g2 = pick_geo(C, L_main, 2, buf_bytes(C, 2, L_max), tc, &s2);
+        if (g2.G && (s2 <= s1 || !g1.G)) S = 2;
+        else S = 1;
     }
+    const uint32_t buf = buf_bytes(C, S, L_max);
     pl->S = S;
-    pl->Rcap = Rcap;
-    for (int i = 0; i < 17; ++i) pl->geo[i] = Geo{0, 0, 0};
-    if (ragged) {
-        for (int L = 4; L <= L_max; L += 2) {
-            TileChoice tl;
-            auto jt = ctx->tiles.find(L);
-            if (jt != ctx->tiles.end()) tl = jt->second;
-            pl->geo[L >> 1] = best_geo(L, Rcap, tl.slab_configs);
-        }
-    } else {
-        pl->geo[L_main >> 1] = gmain;
+    pl->BUF = buf;
+    for (int i = 0; i < 17; ++i) pl->geo[i] = Geo{0, 0, 0, 0};
+    // one lane packing per launch (the epilogue is compiled for it): that of
+    // L_main; every other lattice side of a mixed launch takes its best G
+    // under the same P
+    const Geo gmain = pick_geo(C, L_main, S, buf, tc, nullptr);
+    if (!gmain.G) return VMC_ERR_UNSUPPORTED;
+    const int P = gmain.P;
+    for (int L = 4; L <= L_max; L += 2) {
+        if (!ragged && L != L_main) continue;
+        TileChoice tl;
+        auto jt = ctx->tiles.find(L);
+        if (jt != ctx->tiles.end()) tl = jt->second;
+        tl.lane_cells = P;
+        pl->geo[L >> 1] = (L == L_main) ? gmain : pick_geo(C, L, S, buf, tl, nullptr);
     }
-    pl->smem = wb + (size_t)2 * S * (C / 8) * Rcap * 16 + ctrl;
-    if (pl->smem < 120 * 1024) pl->smem = 120 * 1024;   // keeps one CTA (and one TMEM owner) per SM
+    pl->P = P;
+    pl->slotc = P * C;
+    pl->smem = 2 * (size_t)(18 * C * C) + (size_t)2 * S * buf + ctrl_bytes(L_max);
     if (pl->smem > SMEM_LIMIT) return VMC_ERR_UNSUPPORTED;
     return VMC_OK;
 }
 
-template <int C, bool F16>
-static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, const int64_t *offs,
-                  const int32_t *Ls, int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr,
-                  cudaStream_t st)
+template <int C, bool F16, int NM>
+static int launch_nm(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, const int64_t *offs,
+                     const int32_t *Ls, int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr,
+                     cudaStream_t st)
 {
     Params p;
     p.mode = mode; p.B = B; p.sigma = sigma; p.offs = offs; p.Ls = Ls;
@@ -900,15 +1065,24 @@ static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, c
     p.J1 = ctx->J1; p.J2 = ctx->J2;
     p.wimg = reinterpret_cast<const uint8_t *>(ctx->wimg);
     p.bias32 = ctx->bias32;
-    p.S = pl.S; p.Rcap = pl.Rcap;
-    p.nslots = std::min(MAX_TSLOTS, 512 / (3 * C));
+    p.S = pl.S; p.BUF = pl.BUF;
+    p.slotc = pl.slotc;
+    p.nslots = std::min(MAX_TSLOTS, 512 / pl.slotc);
     for (int i = 0; i < 17; ++i) p.geo[i] = pl.geo[i];
     p.out_a = out_a; p.out_sign = static_cast<int8_t *>(out_b); p.n_nbr = n_nbr;
     p.status = ctx->status; p.counter = ctx->counter;
     p.budget_ns = ctx->wait_budget_ns;
-    auto kfn = tc_eloc_kernel<C, F16>;
-    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-    if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "cudaFuncSetAttribute(tc_eloc)");
+    auto kfn = tc_eloc_kernel<C, F16, NM>;
+    // raise the dynamic shared-memory limit once per device and size, so that
+    // repeat launches (and graph captures after a first call) issue only the
+    // counter reset and the launch
+    static int smem_set[64] = {0};
+    cudaError_t e = cudaSuccess;
+    if (ctx->device < 0 || ctx->device >= 64 || smem_set[ctx->device] < (int)pl.smem) {
+        e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+        if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "cudaFuncSetAttribute(tc_eloc)");
+        if (ctx->device >= 0 && ctx->device < 64) smem_set[ctx->device] = (int)pl.smem;
+    }
     e = cudaMemsetAsync(ctx->counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "counter reset");
     int grid = ctx->sm_count;
@@ -916,6 +1090,20 @@ static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, c
     kfn<<<grid, NTHREADS, pl.smem, st>>>(p);
     ctx->launches += 1;
     return vmc_cuda_check(ctx, cudaGetLastError(), "tc_eloc launch");
+}
+
+template <int C, bool F16>
+static int launch(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, const int64_t *offs,
+                  const int32_t *Ls, int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr,
+                  cudaStream_t st)
+{
+    switch (pl.P * C / 32) {
+        case 1: return launch_nm<C, F16, 1>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st);
+        case 2: return launch_nm<C, F16, 2>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st);
+        case 3: return launch_nm<C, F16, 3>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st);
+        case 4: return launch_nm<C, F16, 4>(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, st);
+        default: return vmc_fail(ctx, VMC_ERR_UNSUPPORTED, "lane packing P=%d with C=%d", pl.P, C);
+    }
 }
 
 static int launch_any(vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, const int64_t *offs,
@@ -972,7 +1160,9 @@ __global__ void umma_selftest_kernel(const uint16_t *A, const uint16_t *Bm, floa
         }
         umma_commit(&bar);
     }
-    int abort_flag = 0, fl = 0, site = 0;
+    __shared__ int abort_flag, fl, site;   // the wait may raise status bits atomically
+    if (tid == 0) { abort_flag = 0; fl = 0; site = 0; }
+    __syncthreads();
     mbar_wait_bounded(&bar, 0, &abort_flag, 1000000000LL, &fl, &site, 0);
     tc_fence_after();
     if (warp < 4) {
@@ -1022,6 +1212,8 @@ __global__ void probe_configs_kernel(int8_t *out, int L, int64_t B)
 }  // namespace tc
 }  // namespace vmc
 
+
+
 using namespace vmc;
 
 int vmc_tc_default_tiles(const vmc_ctx *ctx, int L, TileChoice *t)
@@ -1032,6 +1224,7 @@ int vmc_tc_default_tiles(const vmc_ctx *ctx, int L, TileChoice *t)
     t->slab_configs = pl.geo[L >> 1].G;
     t->slabs = pl.S;
     t->ctas_per_sm = 1;
+    t->lane_cells = pl.geo[L >> 1].P;
     return VMC_OK;
 }
 
@@ -1070,6 +1263,7 @@ extern "C" int vmc_debug_umma_selftest(const uint16_t *A_dev, const uint16_t *B_
     return cudaGetLastError() == cudaSuccess ? VMC_OK : VMC_ERR_CUDA;
 }
 
+
 extern "C" int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream)
 {
     if (!ctx || L < 4 || L > 32 || (L & 1) || probe_B < 1) return VMC_ERR_ARG;
@@ -1092,25 +1286,44 @@ extern "C" int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream)
     int rc = VMC_OK;
     const int saved_L = ctx->L;
     ctx->L = L;
-    for (int S = 1; S <= 2 && rc == VMC_OK; ++S)
-        for (int G = 1; G <= tc::MAX_SLOTS && rc == VMC_OK; ++G) {
+    // candidates: every slab count and geometry, in the order of the MMA
+    // cost model; the best few are timed
+    std::vector<std::pair<double, TileChoice>> cands;
+    for (int S = 1; S <= 2; ++S) {
+        std::vector<tc::Cand> cs;
+        tc::geo_cands(ctx->arch.channels, L, tc::buf_bytes(ctx->arch.channels, S, L), S, cs);
+        for (const tc::Cand &cd : cs) {
             TileChoice t;
             t.slabs = S;
-            t.slab_configs = G;
+            t.slab_configs = cd.g.G;
+            t.lane_cells = cd.g.P;
             t.ctas_per_sm = 1;
-            ctx->tiles[L] = t;
-            tc::Plan pl;
-            if (tc::make_plan(ctx, L, L, false, &pl) != VMC_OK || pl.geo[L >> 1].G != G) continue;
-            float ms = 0.f;
-            for (int rep = 0; rep < 3 && rc == VMC_OK; ++rep) {
-                cudaEventRecord(e0, st);
-                rc = tc::launch_any(ctx, pl, 1, cfg, nullptr, nullptr, probe_B, L, out, nullptr, nullptr, st);
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms, e0, e1);
-            }
-            if (rc == VMC_OK && ms < best_ms) { best_ms = ms; best = t; }
+            cands.push_back({cd.score, t});
         }
+    }
+    std::stable_sort(cands.begin(), cands.end(),
+                     [](const std::pair<double, TileChoice> &a, const std::pair<double, TileChoice> &b) {
+                         return a.first < b.first;
+                     });
+    if (cands.size() > 8) cands.resize(8);
+    for (size_t ci = 0; ci < cands.size() && rc == VMC_OK; ++ci) {
+        const TileChoice t = cands[ci].second;
+        ctx->tiles[L] = t;
+        tc::Plan pl;
+        if (tc::make_plan(ctx, L, L, false, &pl) != VMC_OK || pl.geo[L >> 1].G != t.slab_configs ||
+            pl.geo[L >> 1].P != t.lane_cells)
+            continue;
+        float ms = 0.f, best_rep = 1e30f;
+        for (int rep = 0; rep < 3 && rc == VMC_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = tc::launch_any(ctx, pl, 1, cfg, nullptr, nullptr, probe_B, L, out, nullptr, nullptr, st);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best_rep = std::min(best_rep, ms);
+        }
+        if (rc == VMC_OK && best_rep < best_ms) { best_ms = best_rep; best = t; }
+    }
     ctx->L = saved_L;
     ctx->tiles[L] = best;
     cudaEventDestroy(e0);

@@ -273,7 +273,9 @@ int vmc_set_tiles(vmc_ctx *ctx, int L, const vmc_tiles *tiles)
     t.slab_configs = tiles->slab_configs;
     t.slabs = tiles->slabs;
     t.ctas_per_sm = tiles->ctas_per_sm;
-    if (t.slabs < 0 || t.slabs > 2 || t.slab_configs < 0 || t.slab_configs > 64 || t.ctas_per_sm < 0 || t.ctas_per_sm > 4)
+    t.lane_cells = tiles->lane_cells;
+    if (t.slabs < 0 || t.slabs > 2 || t.slab_configs < 0 || t.slab_configs > 64 || t.ctas_per_sm < 0 ||
+        t.ctas_per_sm > 4 || t.lane_cells < 0 || t.lane_cells > 8)
         return vmc_fail(ctx, VMC_ERR_ARG, "tile choice out of range");
     ctx->tiles[L] = t;
     return VMC_OK;
@@ -291,6 +293,7 @@ int vmc_get_tiles(const vmc_ctx *ctx, int L, vmc_tiles *tiles)
     tiles->slab_configs = t.slab_configs ? t.slab_configs : d.slab_configs;
     tiles->slabs = t.slabs ? t.slabs : d.slabs;
     tiles->ctas_per_sm = t.ctas_per_sm ? t.ctas_per_sm : d.ctas_per_sm;
+    tiles->lane_cells = t.lane_cells ? t.lane_cells : d.lane_cells;
     return VMC_OK;
 }
 

@@ -34,6 +34,7 @@ struct TileChoice {
     int slab_configs = 0;
     int slabs = 0;
     int ctas_per_sm = 0;
+    int lane_cells = 0;
 };
 
 struct vmc_ctx {
@@ -53,7 +54,7 @@ struct vmc_ctx {
     void *wsimtT = nullptr;      // transposed/flipped weights for the backward grad-input conv
     void *bias = nullptr;        // [(D+1)][C] (float or double, matching the SIMT type)
     uint16_t *wimg = nullptr;    // BF16 / FP16 UMMA B-operand images, all layers
-    float *bias32 = nullptr;     // [(D+1)][C] FP32 biases for the tensor-core epilogue
+    float *bias32 = nullptr;     // [(D+1)][C] halved FP32 biases for the tensor-core epilogue
     size_t wimg_bytes = 0;
 
     DevStatus *status = nullptr; // device

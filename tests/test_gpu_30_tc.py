@@ -115,13 +115,49 @@ def test_ragged_equals_uniform_and_oracle():
         np.testing.assert_array_equal(nn.cpu().numpy()[idx[:2]], rn)
 
 
-@pytest.mark.parametrize("G,S", [(1, 1), (1, 2), (3, 2), (2, 1)])
-def test_bf16_tile_choices_agree(G, S):
-    """Every slab geometry gives bitwise the same energies (rows are independent)."""
+def test_ragged_launch_replays_from_a_cuda_graph():
+    """The mixed-size persistent launch captured once in a CUDA graph and
+    replayed gives the eager result bit for bit (the counter reset is part
+    of the captured work)."""
+    w = inputs.WORKLOADS["ragged_8_16"]
+    packed, offs, Ls, theta = inputs.ragged_inputs(w, per_L=8)
+    v = make_ctx(w, theta=theta, L=16)
+    pk, of, Lt = to_dev(packed), to_dev(offs), to_dev(Ls)
+    ref, _ = v.local_energy_ragged(pk, of, Lt, 16)
+    torch.cuda.synchronize()
+    out = torch.empty_like(ref)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        v.local_energy_ragged(pk, of, Lt, 16, out=out, n_nbr=False)
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    assert v.sync_status()[0] == VMC_OK
+
+
+@pytest.mark.parametrize("G,S,P", [(1, 1, 1), (1, 2, 2), (3, 2, 3), (2, 1, 4), (5, 2, 1), (4, 1, 3)])
+def test_bf16_tile_choices_agree(G, S, P):
+    """Every slab geometry and lane packing gives bitwise the same energies:
+    each output cell sums its nine taps in the same order whatever its
+    position in a TMEM lane."""
     w, sig, theta = _small(8, 32, 3, 40, 11)
     v = make_ctx(w, theta=theta)
     ref, _ = v.local_energy(to_dev(sig))
-    v.set_tiles(8, slab_configs=G, slabs=S)
+    v.set_tiles(8, slab_configs=G, slabs=S, lane_cells=P)
+    got, _ = v.local_energy(to_dev(sig))
+    assert v.get_tiles(8)["lane_cells"] == P
+    assert torch.equal(ref, got)
+
+
+@pytest.mark.parametrize("P", [2, 4, 6, 8])
+def test_bf16_c16_lane_packings_agree(P):
+    """C = 16 packs an even number of cells per lane; all give the same bits."""
+    w, sig, theta = _small(8, 16, 2, 24, 17)
+    v = make_ctx(w, theta=theta)
+    ref, _ = v.local_energy(to_dev(sig))
+    v.set_tiles(8, lane_cells=P)
     got, _ = v.local_energy(to_dev(sig))
     assert torch.equal(ref, got)
 

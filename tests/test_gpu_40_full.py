@@ -86,7 +86,13 @@ def test_l16_bf16_mean_energy_vs_fp32(l16):
     assert v32.sync_status()[0] == VMC_OK
     e32 = e32.cpu().numpy()
     N = w.L * w.L
-    assert abs((e[:B] - e32).mean()) / N <= 1e-5
+    # BF16 rounding makes the per-sample error d = E_bf16 - E_fp32 a random
+    # variable (std ~0.1 at L = 16 for this network); the estimator is
+    # unbiased when the mean of d is within a few standard errors of zero.
+    d = e[:B] - e32
+    sem = d.std(ddof=1) / np.sqrt(B)
+    assert abs(d.mean()) <= 4.0 * sem, (d.mean(), sem)
+    assert abs(d.mean()) / N <= 5e-5
     pick = np.random.default_rng(17).choice(B, 2, replace=False)
     re, _ = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
     assert (np.abs(e32[pick] - re) / N).max() <= 1e-6
