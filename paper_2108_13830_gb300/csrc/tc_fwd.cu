@@ -129,6 +129,14 @@ __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" :::
 __host__ __device__ __forceinline__ uint32_t udiv_magic(uint32_t d) { return d == 1u ? 0u : 0xFFFFFFFFu / d + 1u; }
 __device__ __forceinline__ int udiv(int x, uint32_t m) { return m ? (int)__umulhi((uint32_t)x, m) : x; }
 
+// (hi, lo) += x in double-float (TwoSum; lo collects the rounding errors)
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x)
+{
+    const float s = hi + x, bb = s - hi;
+    lo += (hi - (s - bb)) + (x - bb);
+    hi = s;
+}
+
 // two FP32 values -> packed 16-bit pair (low half = a), round to nearest even
 template <bool F16>
 __device__ __forceinline__ uint32_t pack2(float a, float b)
@@ -162,6 +170,26 @@ __device__ __forceinline__ float silu_h(float h)
         return z * (z >= 0.f ? r : e * r);
     } else {
         return fmaf(h, tanh_approx(h), h);
+    }
+}
+
+// SiLU of the pair z = 2 (a, b), packed to 16 bits.  BF16 operands: in FP16
+// pairs, h (1 + tanh h) with the paired hardware tanh (one MUFU op per two
+// values; the FP16 rounding of h and of the product, 2^-11, is below the
+// BF16 rounding of the result, and the tanh error is that of the FP32
+// instruction); FP16 operands: silu_h per value.
+template <bool F16>
+__device__ __forceinline__ uint32_t silu_pack2(float a, float b)
+{
+    if constexpr (F16) {
+        return pack2<true>(silu_h<true>(a), silu_h<true>(b));
+    } else {
+        const __half2 h = __floats2half2_rn(a, b);
+        uint32_t t;
+        asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t *>(&h)));
+        const __half2 y = __hfma2(h, *reinterpret_cast<const __half2 *>(&t), h);
+        const float2 f = __half22float2(y);
+        return pack2<false>(f.x, f.y);
     }
 }
 
@@ -291,10 +319,11 @@ struct Kern {
     Ctrl &c;
     int8_t *spins;
     uint16_t *list;
+    float *bias_s;              // (D + 1) C halved biases
     uint32_t tmem;
 
-    __device__ Kern(const Params &p_, uint8_t *smem_, Ctrl &c_, int8_t *sp, uint16_t *li, uint32_t tm)
-        : p(p_), smem(smem_), c(c_), spins(sp), list(li), tmem(tm) {}
+    __device__ Kern(const Params &p_, uint8_t *smem_, Ctrl &c_, int8_t *sp, uint16_t *li, float *bs, uint32_t tm)
+        : p(p_), smem(smem_), c(c_), spins(sp), list(li), bias_s(bs), tmem(tm) {}
 
     __device__ uint8_t *act_buf(int s, int k) const { return smem + 2 * WB + (size_t)(2 * s + k) * p.BUF; }
 
@@ -461,8 +490,8 @@ struct Kern {
         k.mRW = m.mRW; k.mLP = m.mLP; k.PS = m.PS;
         k.out = smem_u32(act_buf(s, l & 1));
         const int g = ((tid >> 5) >> 2) & (CP8 - 1);
-        const float4 *b4 = reinterpret_cast<const float4 *>(p.bias32 + l * C + g * 8);
-        const float4 lo = __ldg(b4), hi = __ldg(b4 + 1);
+        const float4 *b4 = reinterpret_cast<const float4 *>(bias_s + l * C + g * 8);
+        const float4 lo = b4[0], hi = b4[1];
         k.bias[0] = lo.x; k.bias[1] = lo.y; k.bias[2] = lo.z; k.bias[3] = lo.w;
         k.bias[4] = hi.x; k.bias[5] = hi.y; k.bias[6] = hi.z; k.bias[7] = hi.w;
     }
@@ -503,7 +532,7 @@ struct Kern {
             } else {
                 uint32_t w[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) w[q] = pack2<F16>(silu_h<F16>(h[2 * q]), silu_h<F16>(h[2 * q + 1]));
+                for (int q = 0; q < 4; ++q) w[q] = silu_pack2<F16>(h[2 * q], h[2 * q + 1]);
                 const uint32_t plane = k.out + (uint32_t)(i * CP8 + g) * k.PS;
                 st_shared_v4(plane + (uint32_t)(r + 1) * 16u, w[0], w[1], w[2], w[3]);
                 // circular halo copies: column X -/+ L, row L + 1 / 0, and the corner
@@ -564,25 +593,29 @@ struct Kern {
         for (int task = warp; task < count * POOL_PARTS; task += NEPI_WARPS) {
             const int j = task / POOL_PARTS, part = task - j * POOL_PARTS;
             const int y0 = part * L / POOL_PARTS, y1 = (part + 1) * L / POOL_PARTS;
-            double acc = 0.0;
+            // double-float sums (FP32 pairs, ~2^-48 relative): the FP64 pipe of
+            // this part is slow, and the block sums need more than FP32
+            float hi = 0.f, lo = 0.f;
             int neg = 0, zer = 0;
             if (lane < L) {
                 for (int gg = 0; gg < CP8; ++gg)
                     for (int y = y0; y < y1; ++y) {
                         const int q = gg * NQ + (y + 1) * PW + j * (L + 2) + lane + 1;
-                        acc += (double)partF[q];
+                        df_add(hi, lo, partF[q]);
                         const int nz = partI[q];
                         neg += nz & 0xffff;
                         zer += nz >> 16;
                     }
             }
             for (int o = 16; o > 0; o >>= 1) {
-                acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                df_add(hi, lo, oh);
+                lo += ol;
                 neg += __shfl_xor_sync(0xffffffffu, neg, o);
                 zer += __shfl_xor_sync(0xffffffffu, zer, o);
             }
             if (lane == 0) {
-                c.pool_acc[j][part] = acc;
+                c.pool_acc[j][part] = (double)hi + (double)lo;
                 c.pool_nz[j][part] = (neg & 0xffff) | (zer << 16);
             }
         }
@@ -603,7 +636,10 @@ struct Kern {
                     P.la0 = la;
                     P.sg0 = sg;
                 } else {
-                    const double rho = (double)(sg * P.sg0) * exp(la - P.la0);
+                    // the ratio needs the FP64 difference, not an FP64 exponential:
+                    // expf's ~1e-7 relative error is far below the tolerance
+                    // of the 16-bit network
+                    const double rho = (double)(sg * P.sg0) * (double)__expf((float)(la - P.la0));
                     P.acc += exchange_coef(m.bond[j] & 3, p.J1, p.J2, p.marshall) * rho;
                 }
                 if (--P.remaining == 0) {
@@ -612,7 +648,8 @@ struct Kern {
                 }
             }
         }
-        epi_sync();
+        // no barrier: fill's first step runs on thread 0 too, and the other
+        // threads touch the slab only after fill's barrier
     }
 
     __device__ void finish_parent(const Parent &P)
@@ -681,13 +718,19 @@ struct Kern {
     }
 
     // Fill slab s with the next configurations of the stream; returns count.
+    // Thread 0 decides each step (next parent, or more neighbours of the
+    // current one) and takes configurations into the slab in the same
+    // critical section; the other threads build the im2col rows.  The
+    // caller's barrier (the end of pool_finish's task phase, or the
+    // kernel's start) orders thread 0's first step after every earlier
+    // reader of the slab.
     __device__ int fill(int s, int tid)
     {
         SlabMeta &m = c.slab[s];
-        if (tid == 0) { m.count = 0; m.L = 0; }
-        epi_sync();
+        bool first = true;
         for (;;) {
             if (tid == 0) {
+                if (first) { m.count = 0; m.L = 0; }
                 int act = 2;
                 if (c.abort) {
                     act = 2;   // stop filling; the caller's next abort check ends the epilogue
@@ -713,12 +756,34 @@ struct Kern {
                         break;
                     }
                 }
+                if (act == 0) {
+                    // the slab takes the geometry of the lattice now at the cursor
+                    // (a new parent, or the rest of the previous fill's parent)
+                    if (m.count == 0) set_geometry(m, c.cur_L, p.geo[c.cur_L >> 1]);
+                    if (m.G < 1 || m.G > MAX_SLOTS || m.P != P) {
+                        c.abort = 1;
+                        atomicOr(&p.status->flags, VMC_STATUS_INTERNAL);
+                        m.G = 1;
+                    }
+                    const int n_take = min(m.G - m.count, c.cur_nlist + 1 - c.cur_k);
+                    for (int i = 0; i < n_take; ++i) {
+                        const int kk = c.cur_k + i;
+                        m.parent[m.count + i] = c.cur_parent;
+                        m.bond[m.count + i] = (kk == 0) ? -1 : (int)list[kk - 1];
+                    }
+                    c.seg_first = m.count;
+                    c.seg_n = n_take;
+                    m.count += n_take;
+                    c.cur_k += n_take;
+                }
                 c.action = act;
             }
+            first = false;
             epi_sync();
             const int act = c.action;
             if (act == 2) break;
             if (act == 1) {
+                // a new parent: its spins, then (warp 0) its bond list and ring entry
                 const int Lb = c.new_L;
                 const long long b = c.new_b;
                 const int8_t *sig = p.sigma + (p.offs ? p.offs[b] : b * (long long)Lb * Lb);
@@ -728,64 +793,52 @@ struct Kern {
                     int a1 = 0, a2 = 0, cnt = 0, par = 0;
                     if (p.mode == 1) cnt = build_bond_list_warp(spins, Lb, list, &a1, &a2);
                     else par = marshall_parity_warp(spins, Lb);
-                    if (tid == 0) { c.nb_cnt = cnt; c.nb_a1 = a1; c.nb_a2 = a2; c.nb_par = par; }
+                    __syncwarp();
+                    if (tid == 0) {
+                        const int r = c.ring_head;
+                        c.ring_head = (r + 1) % RING;
+                        Parent &Q = c.ring[r];
+                        if (Q.valid) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); }
+                        Q.b = b;
+                        Q.diag = (p.mode == 1) ? diag_energy(Lb, a1, a2, p.J1, p.J2) : 0.0;
+                        Q.la0 = 0.0; Q.acc = 0.0; Q.sg0 = 0;
+                        Q.nlist = cnt;
+                        Q.remaining = 1 + cnt;
+                        Q.mpar = par;
+                        Q.valid = 1;
+                        Q.L = Lb;
+                        c.cur_parent = r;
+                        c.cur_k = 0;
+                        c.cur_nlist = cnt;
+                        c.cur_L = Lb;
+                    }
                 }
-                epi_sync();
-                if (tid == 0) {
-                    const int r = c.ring_head;
-                    c.ring_head = (r + 1) % RING;
-                    Parent &P = c.ring[r];
-                    if (P.valid) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); }
-                    P.b = b;
-                    P.diag = (p.mode == 1) ? diag_energy(Lb, c.nb_a1, c.nb_a2, p.J1, p.J2) : 0.0;
-                    P.la0 = 0.0; P.acc = 0.0; P.sg0 = 0;
-                    P.nlist = c.nb_cnt;
-                    P.remaining = 1 + c.nb_cnt;
-                    P.mpar = c.nb_par;
-                    P.valid = 1;
-                    P.L = Lb;
-                    c.cur_parent = r;
-                    c.cur_k = 0;
-                    c.cur_nlist = c.nb_cnt;
-                    c.cur_L = Lb;
-                }
-                epi_sync();
+                continue;   // thread 0 takes its configurations next; warp 0's list is
+                            // complete before thread 0 reads it (same warp, after __syncwarp)
             }
-            if (tid == 0) {
-                // the slab takes the geometry of the lattice now at the cursor
-                // (a new parent, or the rest of the previous fill's parent)
-                if (m.count == 0) set_geometry(m, c.cur_L, p.geo[c.cur_L >> 1]);
-                if (m.G < 1 || m.G > MAX_SLOTS || m.P != P) {
-                    c.abort = 1;
-                    atomicOr(&p.status->flags, VMC_STATUS_INTERNAL);
-                    m.G = 1;
-                }
-                const int n_take = min(m.G - m.count, c.cur_nlist + 1 - c.cur_k);
-                for (int i = 0; i < n_take; ++i) {
-                    const int kk = c.cur_k + i;
-                    m.parent[m.count + i] = c.cur_parent;
-                    m.bond[m.count + i] = (kk == 0) ? -1 : (int)list[kk - 1];
-                }
-                c.seg_first = m.count;
-                c.seg_n = n_take;
-                m.count += n_take;
-                c.cur_k += n_take;
-            }
-            epi_sync();
             build_rows(s, c.seg_first, c.seg_n, tid);
-            epi_sync();
             if (m.count >= m.G) break;
+            epi_sync();     // build_rows reads m.bond; thread 0 writes it next
         }
         // cells of no configuration keep whatever the buffer held: they feed
         // only outputs that are dropped
         return m.count;
     }
 
-    __device__ void signal_ready(int s, int tid)
+    // End of a (slab, layer): make this thread's shared-memory writes
+    // visible to the tensor cores, check the CTA-wide abort flag once, and
+    // let the MMA thread start the slab's next layer.  Thread 0 snapshots
+    // c.abort into okf[parity] before the barrier; the next write to the
+    // same entry comes two checks later, after every thread has read it.
+    __device__ bool end_layer(int s, int tid, int &nchk)
     {
         fence_proxy_async_smem();
+        const int kk = (nchk++) & 1;
+        if (tid == 0) c.okf[kk] = c.abort ? 0 : 1;
         epi_sync();
+        if (c.okf[kk] == 0) return false;
         if (tid == 0) mbar_arrive(&c.act_ready[s]);
+        return true;
     }
 
     // Each warp waits (one lane, bounded) for the accumulator slot of the
@@ -820,18 +873,12 @@ struct Kern {
         int slot = 0;
         uint32_t use_par = 0;
         int nchk = 0;
-        // CTA-wide abort check: tid 0 snapshots c.abort into okf[parity]; the
-        // next write to the same slot comes two barriers later, after every
-        // thread has read this one
-        auto go_on = [&]() {
-            const int kk = (nchk++) & 1;
-            if (tid == 0) c.okf[kk] = c.abort ? 0 : 1;
-            epi_sync();
-            return c.okf[kk] != 0;
-        };
+        // all layers' biases into shared memory once
+        for (int i = tid; i < (D + 1) * C; i += NEPI) bias_s[i] = p.bias32[i];
+        epi_sync();
         for (int s = 0; s < p.S; ++s) {
             const int cnt = fill(s, tid);
-            signal_ready(s, tid);
+            if (!end_layer(s, tid, nchk)) return;
             dead[s] = (cnt == 0);
         }
         while (!(dead[0] && dead[1])) {
@@ -843,18 +890,17 @@ struct Kern {
                     load_tctx(s, l, tid, k);
                     if (l < D) {
                         run_tiles<false>(T, slot, use_par, tid, k, nullptr, nullptr);
-                        if (!go_on()) return;
-                        signal_ready(s, tid);
+                        if (!end_layer(s, tid, nchk)) return;
                     } else {
                         // pooling partials go to the buffer layer D - 1 read (its MMAs are
                         // done); the layer-D input buffer is still read by later tiles
                         float *partF = reinterpret_cast<float *>(act_buf(s, p.D & 1));
                         int *partI = reinterpret_cast<int *>(partF + CP8 * k.NQ);
                         run_tiles<true>(T, slot, use_par, tid, k, partF, partI);
-                        if (!go_on()) return;
+                        epi_sync();
                         pool_finish(s, tid, partF, partI, k.NQ);
                         const int cnt = fill(s, tid);
-                        signal_ready(s, tid);
+                        if (!end_layer(s, tid, nchk)) return;
                         dead[s] = (cnt == 0);
                     }
                 }
@@ -871,6 +917,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     Ctrl &c = *reinterpret_cast<Ctrl *>(smem + 2 * Kern<C, F16, NM>::WB + (size_t)2 * p.S * p.BUF);
     int8_t *spins = reinterpret_cast<int8_t *>(&c + 1);
     uint16_t *list = reinterpret_cast<uint16_t *>(spins + ((p.L_max * p.L_max + 15) & ~15));
+    float *bias_s = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(list) + ((8 * p.L_max * p.L_max + 15) & ~15));
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&c.act_ready[i], 1);
@@ -904,7 +951,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    Kern<C, F16, NM> k(p, smem, c, spins, list, c.tmem_base);
+    Kern<C, F16, NM> k(p, smem, c, spins, list, bias_s, c.tmem_base);
     if (warp < MMA_WARP) k.epilogue_role(tid);
     else if ((tid & 31) == 0) k.mma_role();
     tc_fence_before();
@@ -918,9 +965,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
 
 // ------------------------------------------------------------------ planning
 
-static size_t ctrl_bytes(int L_max)
+// control block, spins, bond list, biases
+static size_t ctrl_bytes(int L_max, int C, int D)
 {
-    return sizeof(Ctrl) + ((L_max * L_max + 15) & ~15) + (size_t)4 * L_max * L_max * 2 + 64;
+    return sizeof(Ctrl) + ((L_max * L_max + 15) & ~15) + (((size_t)8 * L_max * L_max + 15) & ~(size_t)15) +
+           (size_t)(D + 1) * C * 4 + 64;
 }
 
 // Slab of G lattices of side L with P cells per TMEM lane: tiles per layer,
@@ -990,10 +1039,10 @@ struct Plan {
     size_t smem;
 };
 
-static uint32_t buf_bytes(int C, int S, int L_max)
+static uint32_t buf_bytes(int C, int S, int L_max, int D)
 {
     const size_t wb = 2 * (size_t)(18 * C * C);
-    const size_t avail = SMEM_LIMIT - wb - ctrl_bytes(L_max) - 1024;
+    const size_t avail = SMEM_LIMIT - wb - ctrl_bytes(L_max, C, D) - 1024;
     return (uint32_t)((avail / (2 * (size_t)S)) & ~(size_t)127);
 }
 
@@ -1015,7 +1064,7 @@ static Geo pick_geo(int C, int L, int S, uint32_t buf, const TileChoice &tc, dou
 
 static int make_plan(const vmc_ctx *ctx, int L_main, int L_max, bool ragged, Plan *pl)
 {
-    const int C = ctx->arch.channels;
+    const int C = ctx->arch.channels, D = ctx->arch.n_layers_cc;
     TileChoice tc;
     auto it = ctx->tiles.find(L_main);
     if (it != ctx->tiles.end()) tc = it->second;
@@ -1023,12 +1072,12 @@ static int make_plan(const vmc_ctx *ctx, int L_main, int L_max, bool ragged, Pla
     if (!S) {
         // the slab count with the better modelled geometry for L_main
         double s1 = 0, s2 = 0;
-        const Geo g1 = pick_geo(C, L_main, 1, buf_bytes(C, 1, L_max), tc, &s1);
-        const Geo g2 = pick_geo(C, L_main, 2, buf_bytes(C, 2, L_max), tc, &s2);
+        const Geo g1 = pick_geo(C, L_main, 1, buf_bytes(C, 1, L_max, D), tc, &s1);
+        const Geo g2 = pick_geo(C, L_main, 2, buf_bytes(C, 2, L_max, D), tc, &s2);
         if (g2.G && (s2 <= s1 || !g1.G)) S = 2;
         else S = 1;
     }
-    const uint32_t buf = buf_bytes(C, S, L_max);
+    const uint32_t buf = buf_bytes(C, S, L_max, D);
     pl->S = S;
     pl->BUF = buf;
     for (int i = 0; i < 17; ++i) pl->geo[i] = Geo{0, 0, 0, 0};
@@ -1048,7 +1097,7 @@ static int make_plan(const vmc_ctx *ctx, int L_main, int L_max, bool ragged, Pla
     }
     pl->P = P;
     pl->slotc = P * C;
-    pl->smem = 2 * (size_t)(18 * C * C) + (size_t)2 * S * buf + ctrl_bytes(L_max);
+    pl->smem = 2 * (size_t)(18 * C * C) + (size_t)2 * S * buf + ctrl_bytes(L_max, C, D);
     if (pl->smem > SMEM_LIMIT) return VMC_ERR_UNSUPPORTED;
     return VMC_OK;
 }
@@ -1291,7 +1340,7 @@ extern "C" int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream)
     std::vector<std::pair<double, TileChoice>> cands;
     for (int S = 1; S <= 2; ++S) {
         std::vector<tc::Cand> cs;
-        tc::geo_cands(ctx->arch.channels, L, tc::buf_bytes(ctx->arch.channels, S, L), S, cs);
+        tc::geo_cands(ctx->arch.channels, L, tc::buf_bytes(ctx->arch.channels, S, L, ctx->arch.n_layers_cc), S, cs);
         for (const tc::Cand &cd : cs) {
             TileChoice t;
             t.slabs = S;
