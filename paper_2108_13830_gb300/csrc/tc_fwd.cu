@@ -198,6 +198,26 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
 }
 
+// stores that happen only where `p` holds (one predicated instruction each)
+__device__ __forceinline__ void st_shared_v4_if(bool p, uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d)
+{
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.v4.b32 [%1], {%2, %3, %4, %5};\n\t}" ::"r"(
+            (uint32_t)p),
+        "r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+        : "memory");
+}
+__device__ __forceinline__ void st_shared_b32_if(bool p, uint32_t addr, uint32_t a)
+{
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.b32 [%1], %2;\n\t}" ::"r"((uint32_t)p),
+                 "r"(addr), "r"(a)
+                 : "memory");
+}
+__device__ __forceinline__ void st_shared_f32_if(bool p, uint32_t addr, float a)
+{
+    st_shared_b32_if(p, addr, __float_as_uint(a));
+}
+
 __device__ __forceinline__ double nan_d() { return __longlong_as_double(0x7ff8000000000000LL); }
 
 // up to four 8-column TMEM loads (columns c, c + S, c + 2 S, c + 3 S of the
@@ -351,49 +371,68 @@ struct Kern {
     __device__ __forceinline__ static int tile_row(const SlabMeta &m, int t) { return m.RW + min(128 * t, m.NRm); }
 
     // ---------------------------------------------------------------- MMA
+    // One MMA whose descriptors are given as (low, high) words: the high
+    // words (stride offset, version) are fixed for a tile, and the entries
+    // below move only the 14-bit start-address field of the low words
+    // (16-byte units; every address stays below 256 KB, so no carry leaves
+    // the field).
+    __device__ __forceinline__ static void mma_lh(uint32_t d, uint32_t alo, uint32_t ahi, uint32_t blo, uint32_t bhi,
+                                                  uint32_t idesc)
+    {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t.reg .b64 da, db;\n\t"
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "mov.b64 da, {%1, %2};\n\t"
+            "mov.b64 db, {%3, %4};\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n\t}" ::"r"(d),
+            "r"(alo), "r"(ahi), "r"(blo), "r"(bhi), "r"(idesc), "r"(1u)
+            : "memory");
+    }
+
     // MMAs of one (ky, h) step, in the order: last cell of the previous lane
     // (tap kx = 0 of output 0), cells 0..P-1 (cell i feeds output
     // i + 1 - kx for the taps kx it reaches inside the lane), first cell of
     // the next lane (tap kx = 2 of output P - 1); every output thus receives
-    // kx = 0, 1, 2 in this order.  ad / bd are the step's descriptors; the
-    // entries move only their start-address fields (16-byte units), which
-    // stay inside [0, 2^14).
-    __device__ __forceinline__ void issue_step(uint32_t dslot, uint64_t ad, uint64_t bd, uint32_t ps16) const
+    // kx = 0, 1, 2 in this order.  a / b: low descriptor words of the step.
+    __device__ __forceinline__ void issue_step(uint32_t dslot, uint32_t a, uint32_t ahi, uint32_t b, uint32_t bhi,
+                                               uint32_t ps16) const
     {
-        umma_bf16(dslot, ad + (uint64_t)((P - 1) * CP8) * ps16 - 1u, bd + 2 * C, idesc_f16kind(128, C, F16), 1);
+        mma_lh(dslot, a + (uint32_t)((P - 1) * CP8) * ps16 - 1u, ahi, b + 2 * C, bhi, idesc_f16kind(128, C, F16));
 #pragma unroll
         for (int i = 0; i < P; ++i) {
             const int jlo = i == 0 ? 1 : 0, jhi = (P - i) < 2 ? (P - i) : 2;
-            umma_bf16(dslot + (uint32_t)((i - 1 + jlo) * C), ad + (uint64_t)(i * CP8) * ps16, bd + (uint64_t)(jlo * C),
-                      idesc_f16kind(128, (jhi - jlo + 1) * C, F16), 1);
+            mma_lh(dslot + (uint32_t)((i - 1 + jlo) * C), a + (uint32_t)(i * CP8) * ps16, ahi, b + (uint32_t)(jlo * C),
+                   bhi, idesc_f16kind(128, (jhi - jlo + 1) * C, F16));
         }
-        umma_bf16(dslot + (uint32_t)((P - 1) * C), ad + 1u, bd, idesc_f16kind(128, C, F16), 1);
+        mma_lh(dslot + (uint32_t)((P - 1) * C), a + 1u, ahi, b, bhi, idesc_f16kind(128, C, F16));
     }
 
     __device__ void issue_tile(int s, int l, int t, int bsel, uint32_t dslot)
     {
         const SlabMeta &m = c.slab[s];
         const uint32_t wb = smem_u32(smem + bsel * WB);
-        const uint32_t PS = m.PS, RW = (uint32_t)m.RW;
+        const uint32_t PS = m.PS, RW = (uint32_t)m.RW, ps16 = PS >> 4;
         const int r0 = tile_row(m, t);
         if (l == 0) {
-            const uint32_t a0 = smem_u32(act_buf(s, 1)) + (uint32_t)(r0 + 1) * 16u;
-            const uint64_t bd = smem_desc(wb, 16 * C, 128), ad = smem_desc(a0, PS, 128);
-            const uint32_t ps16 = PS >> 4;
+            const uint64_t ad = smem_desc(smem_u32(act_buf(s, 1)) + (uint32_t)(r0 + 1) * 16u, PS, 128);
+            const uint64_t bd = smem_desc(wb, 16 * C, 128);
+            const uint32_t alo = (uint32_t)ad, ahi = (uint32_t)(ad >> 32), blo = (uint32_t)bd, bhi = (uint32_t)(bd >> 32);
 #pragma unroll
             for (int i = 0; i < P; ++i)
-                umma_bf16(dslot + (uint32_t)(i * C), ad + (uint64_t)(2 * i) * ps16, bd, idesc_f16kind(128, C, F16), 1);
+                mma_lh(dslot + (uint32_t)(i * C), alo + (uint32_t)(2 * i) * ps16, ahi, blo, bhi, idesc_f16kind(128, C, F16));
         } else {
-            const uint32_t abase = smem_u32(act_buf(s, (l - 1) & 1)) + (uint32_t)(r0 + 1) * 16u;
-            const uint32_t ps16 = PS >> 4;
+            // descriptors at row r0 of the first plane and at the first chunk;
+            // the tile's (ky, h) steps add ky - 1 grid rows, 2 h planes, chunk
+            // ky (C/16) + h of 32 * NCOL bytes
+            const uint64_t ad = smem_desc(smem_u32(act_buf(s, (l - 1) & 1)) + (uint32_t)(r0 + 1) * 16u, PS, 128);
+            const uint64_t bd = smem_desc(wb, 16 * NCOL, 128);
+            const uint32_t alo = (uint32_t)ad, ahi = (uint32_t)(ad >> 32), blo = (uint32_t)bd, bhi = (uint32_t)(bd >> 32);
 #pragma unroll
             for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-                for (int h = 0; h < C / 16; ++h) {
-                    const uint32_t arow = abase + (uint32_t)(ky - 1) * RW * 16u + (uint32_t)h * 2u * PS;
-                    const uint32_t bch = wb + (uint32_t)((ky * (C / 16) + h) * 32 * NCOL);
-                    issue_step(dslot, smem_desc(arow, PS, 128), smem_desc(bch, 16 * NCOL, 128), ps16);
-                }
+                for (int h = 0; h < C / 16; ++h)
+                    issue_step(dslot, alo + (uint32_t)(ky - 1) * RW + (uint32_t)(2 * h) * ps16, ahi,
+                               blo + (uint32_t)((ky * (C / 16) + h) * 2 * NCOL), bhi, ps16);
         }
     }
 
@@ -498,12 +537,15 @@ struct Kern {
 
     // Chunks [M0, M0 + N) of a tile, values in v: for each chunk of an
     // interior cell either store SiLU(z) (with its circular halo copies) or,
-    // for the last layer, the pooling partials.
+    // for the last layer, the pooling partials.  Branch-free: every chunk is
+    // computed and each store carries its own predicate, so the chunks'
+    // arithmetic interleaves.
     template <int M0, int N, bool POOL>
     __device__ __forceinline__ void put_chunks(const float (&v)[N][8], int g4, int r, int Y, int rX, int Yh,
                                                const TileCtx &k, float *partF, int *partI)
     {
         const int L = k.L;
+        const bool row_in = (Y >= 1) & (Y <= L);
 #pragma unroll
         for (int mm = 0; mm < N; ++mm) {
             const int m = M0 + mm;
@@ -513,7 +555,7 @@ struct Kern {
             const int X = P * rX + i;
             const int j = udiv(X, k.mLP);
             const int x = X - j * (L + 2) - 1;
-            if (x < 0 || x >= L || j >= k.count) continue;
+            const bool valid = row_in & (x >= 0) & (x < L) & (j < k.count);
             float h[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) h[q] = v[mm][q] + k.bias[q];
@@ -526,30 +568,26 @@ struct Kern {
                     neg += (h[q] < 0.f);
                     zer += (h[q] == 0.f);
                 }
-                const int qc = Y * k.PW + X;
-                partF[g * k.NQ + qc] = sl + 8.0f;   // log2|z| = log2|h| + 1 per channel
-                partI[g * k.NQ + qc] = neg | (zer << 16);
+                const int qc = g * k.NQ + Y * k.PW + X;
+                // log2|z| = log2|h| + 1 per channel
+                st_shared_f32_if(valid, smem_u32(partF + qc), sl + 8.0f);
+                st_shared_b32_if(valid, smem_u32(partI + qc), (uint32_t)(neg | (zer << 16)));
             } else {
                 uint32_t w[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) w[q] = silu_pack2<F16>(h[2 * q], h[2 * q + 1]);
                 const uint32_t plane = k.out + (uint32_t)(i * CP8 + g) * k.PS;
-                st_shared_v4(plane + (uint32_t)(r + 1) * 16u, w[0], w[1], w[2], w[3]);
                 // circular halo copies: column X -/+ L, row L + 1 / 0, and the corner
                 const int hx = (x == 0) ? L : ((x == L - 1) ? -L : 0);
-                uint32_t hplane = 0;
-                int hr = 0;
-                if (hx) {
-                    const int X2 = X + hx;
-                    const int xr = X2 / P;
-                    hplane = k.out + (uint32_t)((X2 - xr * P) * CP8 + g) * k.PS;
-                    hr = xr;
-                    st_shared_v4(hplane + (uint32_t)(Y * k.RW + hr + 1) * 16u, w[0], w[1], w[2], w[3]);
-                }
-                if (Yh >= 0) {
-                    st_shared_v4(plane + (uint32_t)(Yh * k.RW + rX + 1) * 16u, w[0], w[1], w[2], w[3]);
-                    if (hx) st_shared_v4(hplane + (uint32_t)(Yh * k.RW + hr + 1) * 16u, w[0], w[1], w[2], w[3]);
-                }
+                const int X2 = X + hx;
+                const int xr = X2 / P;
+                const uint32_t hplane = k.out + (uint32_t)((X2 - xr * P) * CP8 + g) * k.PS;
+                const int Yv = Yh < 0 ? Y : Yh;
+                st_shared_v4_if(valid, plane + (uint32_t)(r + 1) * 16u, w[0], w[1], w[2], w[3]);
+                st_shared_v4_if(valid & (hx != 0), hplane + (uint32_t)(Y * k.RW + xr + 1) * 16u, w[0], w[1], w[2], w[3]);
+                st_shared_v4_if(valid & (Yh >= 0), plane + (uint32_t)(Yv * k.RW + rX + 1) * 16u, w[0], w[1], w[2], w[3]);
+                st_shared_v4_if(valid & (hx != 0) & (Yh >= 0), hplane + (uint32_t)(Yv * k.RW + xr + 1) * 16u, w[0],
+                                w[1], w[2], w[3]);
             }
         }
     }
@@ -572,7 +610,7 @@ struct Kern {
         if (ok) {
             tmem_ld_chunks<NM, 32>(ta, v);
             tmem_zero_chunks_async<NM, 32>(ta);
-            if (Y >= 1 && Y <= L) put_chunks<0, NM, POOL>(v, g4, r, Y, rX, Yh, k, partF, partI);
+            put_chunks<0, NM, POOL>(v, g4, r, Y, rX, Yh, k, partF, partI);
             __syncwarp();
             tmem_wait_st();
         }
@@ -825,27 +863,34 @@ struct Kern {
         return m.count;
     }
 
-    // End of a (slab, layer): make this thread's shared-memory writes
-    // visible to the tensor cores, check the CTA-wide abort flag once, and
-    // let the MMA thread start the slab's next layer.  Thread 0 snapshots
-    // c.abort into okf[parity] before the barrier; the next write to the
-    // same entry comes two checks later, after every thread has read it.
-    __device__ bool end_layer(int s, int tid, int &nchk)
+    // End of a (slab, layer) for this warp: make its shared-memory writes
+    // visible to the tensor cores and arrive on the slab's ready barrier
+    // (one arrival per epilogue warp), so that no warp waits for the others.
+    // A warp cannot arrive for layer l + 1 before every warp has arrived for
+    // layer l: its tiles of layer l + 1 need MMAs that wait for that phase.
+    __device__ void warp_done(int s, int tid)
     {
         fence_proxy_async_smem();
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&c.act_ready[s]);
+    }
+
+    // CTA-wide abort check at a barrier: thread 0 snapshots c.abort into
+    // okf[parity] before the barrier; the next write to the same entry comes
+    // two checks later, after every thread has read it.
+    __device__ bool cta_check(int tid, int &nchk)
+    {
         const int kk = (nchk++) & 1;
         if (tid == 0) c.okf[kk] = c.abort ? 0 : 1;
         epi_sync();
-        if (c.okf[kk] == 0) return false;
-        if (tid == 0) mbar_arrive(&c.act_ready[s]);
-        return true;
+        return c.okf[kk] != 0;
     }
 
     // Each warp waits (one lane, bounded) for the accumulator slot of the
-    // next tile.  A warp whose wait fails keeps going through the tile loop
-    // without touching TMEM, so every named barrier still sees all
-    // participants; the whole epilogue returns together at the next CTA-wide
-    // check of c.abort.
+    // next tile.  A warp whose wait fails (timeout or abort) keeps going
+    // through the tile loops without touching TMEM, so every named barrier
+    // still sees all participants; the whole epilogue returns together at
+    // the next CTA-wide check (the pooling step of a slab).
     __device__ __forceinline__ bool wait_tile(int slot, uint32_t par, int tid)
     {
         int ok = 0;
@@ -878,7 +923,7 @@ struct Kern {
         epi_sync();
         for (int s = 0; s < p.S; ++s) {
             const int cnt = fill(s, tid);
-            if (!end_layer(s, tid, nchk)) return;
+            warp_done(s, tid);
             dead[s] = (cnt == 0);
         }
         while (!(dead[0] && dead[1])) {
@@ -890,17 +935,19 @@ struct Kern {
                     load_tctx(s, l, tid, k);
                     if (l < D) {
                         run_tiles<false>(T, slot, use_par, tid, k, nullptr, nullptr);
-                        if (!end_layer(s, tid, nchk)) return;
+                        warp_done(s, tid);
                     } else {
                         // pooling partials go to the buffer layer D - 1 read (its MMAs are
                         // done); the layer-D input buffer is still read by later tiles
                         float *partF = reinterpret_cast<float *>(act_buf(s, p.D & 1));
                         int *partI = reinterpret_cast<int *>(partF + CP8 * k.NQ);
                         run_tiles<true>(T, slot, use_par, tid, k, partF, partI);
-                        epi_sync();
+                        // every warp's partials are in place; a timed-out or
+                        // failed CTA returns here, all warps together
+                        if (!cta_check(tid, nchk)) return;
                         pool_finish(s, tid, partF, partI, k.NQ);
                         const int cnt = fill(s, tid);
-                        if (!end_layer(s, tid, nchk)) return;
+                        warp_done(s, tid);
                         dead[s] = (cnt == 0);
                     }
                 }
@@ -920,7 +967,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     float *bias_s = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(list) + ((8 * p.L_max * p.L_max + 15) & ~15));
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            mbar_init(&c.act_ready[i], 1);
+            mbar_init(&c.act_ready[i], NEPI_WARPS);   // one arrival per epilogue warp
             mbar_init(&c.w_full[i], 1);
             mbar_init(&c.w_empty[i], 1);
         }
