@@ -30,6 +30,24 @@ sys.path.insert(0, ROOT)
 
 from paper_2108_13830_gb300 import inputs, replicas  # noqa: E402
 
+
+def tc_traffic(samples):
+    """DRAM bytes of one tensor-core E_loc launch over `samples` samples, from
+    the ncu capture summarised in profiles/tc_eloc_L24_dram.md (scaled by the
+    sample count, which the traffic grows with), or None once the kernel
+    source differs from the one the counters were taken on."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "tc_eloc_L24_dram.md")
+    src = os.path.join(ROOT, "paper_2108_13830_gb300", "csrc", "tc_fwd.cu")
+    try:
+        m = re.search(r"traffic: kernel=\S+ sha256=([0-9a-f]{64}) samples=(\d+) dram_bytes=(\d+)", open(path).read())
+        if not m or hashlib.sha256(open(src, "rb").read()).hexdigest() != m.group(1):
+            return None
+        return int(m.group(3)) * samples / int(m.group(2))
+    except OSError:
+        return None
+
 METRIC = "E_loc+O_k samples/sec at L=16,24 (BF16-TC vs FP32 plain); roofline %"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
@@ -296,13 +314,7 @@ def main():
     peak_t = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
     eloc_mean = statistics.mean(eloc_ms)
     achieved = flops_eloc / (eloc_mean / 1e3) / 1e12
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        try:
-            traffic = json.load(open(tp)).get(f"tc_eloc_{w.name}")
-        except Exception:
-            traffic = None
+    traffic = tc_traffic(B) if w.name == "L24_bf16_sr" else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
                 "frac": achieved / peak_t, "traffic": traffic, "kernel": "tc_eloc_kernel<32>",
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
