@@ -51,8 +51,9 @@ namespace tc {
 
 constexpr int NEPI_WARPS = 16;
 constexpr int NEPI = NEPI_WARPS * 32;     // epilogue threads
-constexpr int MMA_WARP = NEPI_WARPS;
-constexpr int NTHREADS = NEPI + 32;
+constexpr int MMA_WARP = NEPI_WARPS;       // first of the MMA-issuing warps
+constexpr int NMMA = 2;                    // MMA-issuing warps (alternate tiles)
+constexpr int NTHREADS = NEPI + 32 * NMMA;
 constexpr int MAX_SLOTS = 16;             // configurations per slab
 constexpr int MAX_P = 8;                  // cells per TMEM lane (P C <= 128 accumulator columns)
 constexpr int POOL_PARTS = 8;             // row blocks of a lattice summed separately by the pooling
@@ -101,8 +102,8 @@ struct SlabMeta {
     int bond[MAX_SLOTS];
 };
 
-struct Ctrl {
-    uint64_t act_ready[2], w_full[2], w_empty[2], drain;
+struct __align__(16) Ctrl {   // 16-byte size: the arrays placed after it are read as float4
+    uint64_t act_ready[2], w_full[2], w_empty[2], drain[NMMA];
     uint64_t t_full[MAX_TSLOTS], t_empty[MAX_TSLOTS];
     uint32_t tmem_base;
     int abort;
@@ -120,6 +121,8 @@ struct Ctrl {
     int pool_nz[MAX_SLOTS][POOL_PARTS];
     Parent ring[RING];
 };
+
+static_assert(sizeof(Ctrl) % 16 == 0, "control block size keeps what follows it 16-byte aligned");
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
@@ -436,7 +439,16 @@ struct Kern {
         }
     }
 
-    __device__ void mma_role()
+    // MMA issue.  NMMA warps (one lane each) walk the same tile sequence
+    // (layers, slabs, tiles) and issue alternate tiles: tile n goes to
+    // warp n % NMMA, into TMEM slot n % nslots.  A single thread issues a
+    // tcgen05.mma only every ~55 cycles, slower than the tensor cores
+    // consume these narrow MMAs; two issuers reach the shared-memory operand
+    // bound.  Each tile's MMAs come from one thread in a fixed order, so the
+    // results do not depend on the split.  Both warps wait for the slab and
+    // weight barriers; each commits its MMAs of a weight step to w_empty
+    // (two arrivals per phase), and warp 0 alone issues the weight copies.
+    __device__ void mma_role(int mw)
     {
         const int D = p.D, R = p.nslots;
         int issued[2] = {0, 0}, waited[2] = {0, 0};
@@ -448,14 +460,15 @@ struct Kern {
             bulk_g2s(smem + bsel * WB, p.wimg + tc_wimg_offset(C, l), bytes, &c.w_full[bsel]);
             issued[bsel]++;
         };
-        issue_w(0);
-        issue_w(1);
+        if (mw == 0) {
+            issue_w(0);
+            issue_w(1);
+        }
         bool dead[2] = {false, p.S < 2};
         int cnt[2] = {0, 0};
         uint32_t ph_ar[2] = {0, 0};
         long long step = 0;           // weight step
-        int slot = 0;                 // TMEM slot of the next tile, and the parity of its use
-        uint32_t use_par = 0;
+        long long n = 0;              // tile sequence number
         bool ok = true;
         while (ok && !(dead[0] && dead[1])) {
             for (int l = 0; l <= D && ok; ++l) {
@@ -473,21 +486,23 @@ struct Kern {
                     if (!any) {
                         const int bsel = (int)(step & 1);
                         if (!wait_bar(&c.w_full[bsel], (uint32_t)((step >> 1) & 1), 2)) { ok = false; break; }
-                        waited[bsel]++;
+                        if (mw == 0) waited[bsel]++;
                         any = true;
                     }
                     const int T = *(volatile int *)&c.slab[s].T;
-                    for (int t = 0; t < T; ++t) {
+                    for (int t = 0; t < T; ++t, ++n) {
+                        if ((int)(n % NMMA) != mw) continue;
+                        const int slot = (int)(n % R);
+                        const uint32_t use_par = (uint32_t)((n / R) & 1);
                         if (!wait_bar(&c.t_empty[slot], use_par ^ 1u, 3)) { ok = false; break; }
                         tc_fence_after();
                         issue_tile(s, l, t, (int)(step & 1), tmem + (uint32_t)(slot * p.slotc));
                         umma_commit(&c.t_full[slot]);
-                        if (++slot == R) { slot = 0; use_par ^= 1u; }
                     }
                 }
                 if (!ok || !any) break;
                 umma_commit(&c.w_empty[step & 1]);
-                if (step >= 1) {
+                if (step >= 1 && mw == 0) {
                     if (!wait_bar(&c.w_empty[(step - 1) & 1], (uint32_t)(((step - 1) >> 1) & 1), 4)) { ok = false; break; }
                     issue_w(step + 1);
                 }
@@ -504,8 +519,8 @@ struct Kern {
                     break;
                 waited[bsel]++;
             }
-        umma_commit(&c.drain);
-        mbar_wait_bounded(&c.drain, 0, &dummy_abort, cb, &p.status->flags, &p.status->timeout_site, 6);
+        umma_commit(&c.drain[mw]);
+        mbar_wait_bounded(&c.drain[mw], 0, &dummy_abort, cb, &p.status->flags, &p.status->timeout_site, 6);
     }
 
     // ---------------------------------------------------------------- epilogue
@@ -962,20 +977,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x, warp = tid >> 5;
     Ctrl &c = *reinterpret_cast<Ctrl *>(smem + 2 * Kern<C, F16, NM>::WB + (size_t)2 * p.S * p.BUF);
-    int8_t *spins = reinterpret_cast<int8_t *>(&c + 1);
+    // spins, bond list and biases follow the control block, each 16-byte
+    // aligned (the biases are read as float4)
+    int8_t *spins = reinterpret_cast<int8_t *>((reinterpret_cast<uintptr_t>(&c + 1) + 15) & ~(uintptr_t)15);
     uint16_t *list = reinterpret_cast<uint16_t *>(spins + ((p.L_max * p.L_max + 15) & ~15));
     float *bias_s = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(list) + ((8 * p.L_max * p.L_max + 15) & ~15));
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(&c.act_ready[i], NEPI_WARPS);   // one arrival per epilogue warp
             mbar_init(&c.w_full[i], 1);
-            mbar_init(&c.w_empty[i], 1);
+            mbar_init(&c.w_empty[i], NMMA);   // one commit per MMA-issuing warp
         }
         for (int i = 0; i < MAX_TSLOTS; ++i) {
             mbar_init(&c.t_full[i], 1);
             mbar_init(&c.t_empty[i], NEPI_WARPS);   // one arrival per epilogue warp
         }
-        mbar_init(&c.drain, 1);
+        for (int i = 0; i < NMMA; ++i) mbar_init(&c.drain[i], 1);
         c.abort = 0;
         c.cur_parent = -1; c.cur_k = 0; c.cur_nlist = -1; c.cur_L = 0;
         for (int i = 0; i < 2; ++i) { c.slab[i].count = 0; c.slab[i].L = 0; c.slab[i].G = 0; c.slab[i].T = 0; }
@@ -1000,7 +1017,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     tc_fence_after();
     Kern<C, F16, NM> k(p, smem, c, spins, list, bias_s, c.tmem_base);
     if (warp < MMA_WARP) k.epilogue_role(tid);
-    else if ((tid & 31) == 0) k.mma_role();
+    else if ((tid & 31) == 0) k.mma_role(warp - MMA_WARP);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
