@@ -56,7 +56,7 @@ constexpr int NMMA = 2;                    // MMA-issuing warps (alternate tiles
 constexpr int NTHREADS = NEPI + 32 * NMMA;
 constexpr int MAX_SLOTS = 16;             // configurations per slab
 constexpr int MAX_P = 8;                  // cells per TMEM lane (P C <= 128 accumulator columns)
-constexpr int POOL_PARTS = 8;             // row blocks of a lattice summed separately by the pooling
+constexpr int POOL_PARTS = 16;             // row blocks of a lattice summed separately by the pooling
 constexpr int RING = 32;                  // parents in flight per CTA
 constexpr int MAX_TSLOTS = 16;            // TMEM accumulator slots
 constexpr int SMEM_LIMIT = 232448;
@@ -117,7 +117,8 @@ struct __align__(16) Ctrl {   // 16-byte size: the arrays placed after it are re
     int seg_first, seg_n;
     int nb_cnt, nb_a1, nb_a2, nb_par;
     SlabMeta slab[2];
-    double pool_acc[MAX_SLOTS][POOL_PARTS];   // per-configuration pooling partials
+    float pool_hi[MAX_SLOTS][POOL_PARTS];     // per-configuration pooling partials (double-float)
+    float pool_lo[MAX_SLOTS][POOL_PARTS];
     int pool_nz[MAX_SLOTS][POOL_PARTS];
     Parent ring[RING];
 };
@@ -651,14 +652,17 @@ struct Kern {
             float hi = 0.f, lo = 0.f;
             int neg = 0, zer = 0;
             if (lane < L) {
-                for (int gg = 0; gg < CP8; ++gg)
-                    for (int y = y0; y < y1; ++y) {
-                        const int q = gg * NQ + (y + 1) * PW + j * (L + 2) + lane + 1;
+                for (int y = y0; y < y1; ++y) {
+                    const int q0 = (y + 1) * PW + j * (L + 2) + lane + 1;
+#pragma unroll
+                    for (int gg = 0; gg < CP8; ++gg) {
+                        const int q = gg * NQ + q0;
                         df_add(hi, lo, partF[q]);
                         const int nz = partI[q];
                         neg += nz & 0xffff;
                         zer += nz >> 16;
                     }
+                }
             }
             for (int o = 16; o > 0; o >>= 1) {
                 const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
@@ -668,20 +672,23 @@ struct Kern {
                 zer += __shfl_xor_sync(0xffffffffu, zer, o);
             }
             if (lane == 0) {
-                c.pool_acc[j][part] = (double)hi + (double)lo;
+                c.pool_hi[j][part] = hi;
+                c.pool_lo[j][part] = lo;
                 c.pool_nz[j][part] = (neg & 0xffff) | (zer << 16);
             }
         }
         epi_sync();
         if (tid == 0) {
             for (int j = 0; j < count; ++j) {
-                double acc = 0.0;
+                float hi = 0.f, lo = 0.f;
                 int neg = 0, zer = 0;
                 for (int part = 0; part < POOL_PARTS; ++part) {
-                    acc += c.pool_acc[j][part];
+                    df_add(hi, lo, c.pool_hi[j][part]);
+                    lo += c.pool_lo[j][part];
                     neg += c.pool_nz[j][part] & 0xffff;
                     zer += c.pool_nz[j][part] >> 16;
                 }
+                const double acc = (double)hi + (double)lo;
                 const double la = zer ? -INFINITY : acc * 0.69314718055994530942;
                 const int sg = zer ? 0 : ((neg & 1) ? -1 : 1);
                 Parent &P = c.ring[m.parent[j]];
@@ -731,36 +738,36 @@ struct Kern {
 
     // Build the embedding-layer im2col rows of slots [first, first+n): nine
     // spins of sigma' around each interior cell, 16 values in two planes
-    // (planes 2 i, 2 i + 1 for cell i of its lane).
+    // (planes 2 i, 2 i + 1 for cell i of its lane).  One warp per lattice
+    // row, lane = x (L <= 32), so no per-cell division.
     __device__ void build_rows(int s, int first, int n, int tid)
     {
         const SlabMeta &m = c.slab[s];
-        const int L = m.L, PW = m.PW, npix = L * L;
+        const int L = m.L, PW = m.PW;
         const uint32_t a0 = smem_u32(act_buf(s, 1));
         const uint32_t PS = m.PS;
         const uint32_t up = F16 ? 0x3C00u : 0x3F80u, dn = F16 ? 0xBC00u : 0xBF80u;
-        for (int idx = tid; idx < n * npix; idx += NEPI) {
-            const int jj = first + idx / npix, pix = idx - (idx / npix) * npix;
-            const int y = pix / L, x = pix - y * L;
+        const int warp = tid >> 5, x = tid & 31;
+        const int xl = x == 0 ? L - 1 : x - 1, xr = x == L - 1 ? 0 : x + 1;
+        for (int row = warp; row < n * L; row += NEPI_WARPS) {
+            const int jrel = row / L, y = row - jrel * L;
+            if (x >= L) continue;
+            const int jj = first + jrel;
             const int bond = m.bond[jj];
             int bi = -1, bj = -1;
             if (bond >= 0) { bi = bond >> 2; bj = bond_partner(L, bi, bond & 3); }
+            const int ym = y == 0 ? L - 1 : y - 1, yp = y == L - 1 ? 0 : y + 1;
+            const int rows3[3] = {ym * L, y * L, yp * L};
+            const int cols3[3] = {xl, x, xr};
             uint32_t h[9];
 #pragma unroll
-            for (int ky = 0; ky < 3; ++ky) {
-                int sy = y + ky - 1;
-                sy = sy < 0 ? sy + L : (sy >= L ? sy - L : sy);
+            for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
                 for (int kx = 0; kx < 3; ++kx) {
-                    int sx = x + kx - 1;
-                    sx = sx < 0 ? sx + L : (sx >= L ? sx - L : sx);
-                    const int site = sy * L + sx;
-                    int v = spins[site];
-                    if (site == bi) v = spins[bj];
-                    else if (site == bj) v = spins[bi];
-                    h[ky * 3 + kx] = v > 0 ? up : dn;
+                    const int site = rows3[ky] + cols3[kx];
+                    const int src = site == bi ? bj : (site == bj ? bi : site);
+                    h[ky * 3 + kx] = spins[src] > 0 ? up : dn;
                 }
-            }
             const int q = (y + 1) * PW + jj * (L + 2) + x + 1;
             const int r = q / P;
             const int i = q - r * P;
