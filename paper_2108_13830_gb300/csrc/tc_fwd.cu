@@ -562,15 +562,25 @@ struct Kern {
     {
         const int L = k.L;
         const bool row_in = (Y >= 1) & (Y <= L);
+        const int g = g4 & (CP8 - 1);
+        // the lane's P cells are consecutive in X: configuration j and column x
+        // of the first, then advance (wrapping into the next configuration)
+        const int X0 = P * rX + ((CP8 == 4) ? M0 : 2 * M0 + (g4 >> 1));
+        int j = udiv(X0, k.mLP);
+        int x = X0 - j * (L + 2) - 1;
+        const uint32_t outg = k.out + (uint32_t)g * k.PS;
+        const int Yv = Yh < 0 ? Y : Yh;
+        const uint32_t rowY = (uint32_t)(Y * k.RW + 1) * 16u, rowV = (uint32_t)(Yv * k.RW + 1) * 16u;
 #pragma unroll
         for (int mm = 0; mm < N; ++mm) {
             const int m = M0 + mm;
             // chunk k = g4 + 4 m: cell i, channel plane g
             const int i = (CP8 == 4) ? m : 2 * m + (g4 >> 1);
-            const int g = g4 & (CP8 - 1);
+            if (mm > 0) {
+                x += (CP8 == 4) ? 1 : 2;
+                if (x > L) { x -= L + 2; ++j; }
+            }
             const int X = P * rX + i;
-            const int j = udiv(X, k.mLP);
-            const int x = X - j * (L + 2) - 1;
             const bool valid = row_in & (x >= 0) & (x < L) & (j < k.count);
             float h[8];
 #pragma unroll
@@ -592,18 +602,17 @@ struct Kern {
                 uint32_t w[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) w[q] = silu_pack2<F16>(h[2 * q], h[2 * q + 1]);
-                const uint32_t plane = k.out + (uint32_t)(i * CP8 + g) * k.PS;
+                const uint32_t plane = outg + (uint32_t)(i * CP8) * k.PS;
                 // circular halo copies: column X -/+ L, row L + 1 / 0, and the corner
                 const int hx = (x == 0) ? L : ((x == L - 1) ? -L : 0);
                 const int X2 = X + hx;
                 const int xr = X2 / P;
-                const uint32_t hplane = k.out + (uint32_t)((X2 - xr * P) * CP8 + g) * k.PS;
-                const int Yv = Yh < 0 ? Y : Yh;
+                const uint32_t hplane = outg + (uint32_t)((X2 - xr * P) * CP8) * k.PS + (uint32_t)xr * 16u;
+                const uint32_t rr = (uint32_t)rX * 16u;
                 st_shared_v4_if(valid, plane + (uint32_t)(r + 1) * 16u, w[0], w[1], w[2], w[3]);
-                st_shared_v4_if(valid & (hx != 0), hplane + (uint32_t)(Y * k.RW + xr + 1) * 16u, w[0], w[1], w[2], w[3]);
-                st_shared_v4_if(valid & (Yh >= 0), plane + (uint32_t)(Yv * k.RW + rX + 1) * 16u, w[0], w[1], w[2], w[3]);
-                st_shared_v4_if(valid & (hx != 0) & (Yh >= 0), hplane + (uint32_t)(Yv * k.RW + xr + 1) * 16u, w[0],
-                                w[1], w[2], w[3]);
+                st_shared_v4_if(valid & (hx != 0), hplane + rowY, w[0], w[1], w[2], w[3]);
+                st_shared_v4_if(valid & (Yh >= 0), plane + rowV + rr, w[0], w[1], w[2], w[3]);
+                st_shared_v4_if(valid & (hx != 0) & (Yh >= 0), hplane + rowV, w[0], w[1], w[2], w[3]);
             }
         }
     }
