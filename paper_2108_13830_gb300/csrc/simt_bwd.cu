@@ -64,8 +64,12 @@ struct StoreGradSilu {
     }
 };
 
+// 512 threads: one CTA per SM fits (two C-channel planes of shared memory),
+// and the per-sample work is latency-bound at fewer warps
+constexpr int BWD_THREADS = 512;
+
 template <typename T, int CO, typename OutT>
-__global__ void __launch_bounds__(256) simt_bwd_kernel(BwdParams p)
+__global__ void __launch_bounds__(BWD_THREADS) simt_bwd_kernel(BwdParams p)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int8_t *s = reinterpret_cast<int8_t *>(smem);
@@ -128,10 +132,12 @@ __global__ void __launch_bounds__(256) simt_bwd_kernel(BwdParams p)
                 halo_fill(ibuf, C, L, PP);
             }
             __syncthreads();
-            // per-sample weight gradient: item = (block of 4 output channels, input channel)
+            // per-sample weight gradient: item = (block of 4 output channels, input
+            // channel), on two adjacent lanes that take the even and odd rows
             OutT *dW = Ob + vmc_woffset(C, l);
             const int nitems = (C / 4) * cin;
-            for (int it = threadIdx.x; it < nitems; it += blockDim.x) {
+            for (int it2 = threadIdx.x; it2 < 2 * nitems; it2 += blockDim.x) {
+                const int it = it2 >> 1, half = it2 & 1;
                 const int cb = it / cin, ci = it - cb * cin;
                 T acc[4][9];
 #pragma unroll
@@ -140,7 +146,7 @@ __global__ void __launch_bounds__(256) simt_bwd_kernel(BwdParams p)
                     for (int t = 0; t < 9; ++t) acc[j][t] = T(0);
                 const T *ip = ibuf + ci * PP;
                 const T *gp = gbuf + cb * 4 * PP;
-                for (int y = 0; y < L; ++y)
+                for (int y = half; y < L; y += 2)
                     for (int x = 0; x < L; ++x) {
                         T a[9];
 #pragma unroll
@@ -154,11 +160,19 @@ __global__ void __launch_bounds__(256) simt_bwd_kernel(BwdParams p)
                             for (int t = 0; t < 9; ++t) acc[j][t] = fma(g, a[t], acc[j][t]);
                         }
                     }
+                // both lanes of the pair are active (2 nitems is even)
+                const unsigned pm = __activemask();
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
 #pragma unroll
-                    for (int t = 0; t < 9; ++t)
-                        dW[((cb * 4 + j) * cin + ci) * 9 + t] = (OutT)acc[j][t];
+                    for (int t = 0; t < 9; ++t) acc[j][t] += __shfl_xor_sync(pm, acc[j][t], 1);
+                if (half == 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int t = 0; t < 9; ++t)
+                            dW[((cb * 4 + j) * cin + ci) * 9 + t] = (OutT)acc[j][t];
+                }
             }
             for (int c = threadIdx.x; c < C; c += blockDim.x) {
                 T acc = T(0);
@@ -193,7 +207,7 @@ static int launch_bwd(vmc_ctx *ctx, const int8_t *sigma, int64_t B, void *O, cud
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "cudaFuncSetAttribute(simt_bwd)");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, BWD_THREADS, smem);
     if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "occupancy(simt_bwd)");
     if (per_sm < 1) return vmc_fail(ctx, VMC_ERR_UNSUPPORTED, "backward does not fit on an SM (L=%d, C=%d)", L, C);
     int64_t grid = (int64_t)per_sm * ctx->sm_count;
@@ -205,7 +219,7 @@ static int launch_bwd(vmc_ctx *ctx, const int8_t *sigma, int64_t B, void *O, cud
     p.L = L; p.C = C; p.D = D; p.B = B; p.n = ctx->n;
     p.sigma = sigma; p.W = ctx->wsimt; p.WT = ctx->wsimtT; p.bias = ctx->bias;
     p.scratch = ctx->ws; p.O = O;
-    kfn<<<(unsigned)grid, 256, smem, st>>>(p);
+    kfn<<<(unsigned)grid, BWD_THREADS, smem, st>>>(p);
     ctx->launches += 1;
     return vmc_cuda_check(ctx, cudaGetLastError(), "simt_bwd launch");
 }
