@@ -14,6 +14,8 @@ checked at the L = 16 and L = 24 workloads (test_gpu_40_full.py).
 Networks with only 2-3 layers produce last-layer outputs near zero, where
 any 16-bit rounding moves log|psi| by O(1); they are used only for checks
 that hold exactly (translation, tile choices)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -63,6 +65,38 @@ def test_tc_logpsi_small(prec, tol):
     ra, rs = oracle.logpsi(w.L, w.C, w.D, theta, sig)
     np.testing.assert_array_equal(sg.cpu().numpy().astype(np.int32), rs)
     assert np.abs(la.cpu().numpy() - ra).max() <= tol
+
+
+@pytest.fixture(scope="module")
+def l32_reference():
+    """Inputs of the L = 32 check (the same for both precisions) and the
+    oracle's log|psi| of all samples and E_loc of the first, computed once."""
+    w, sig, theta = _small(32, 32, 6, 6, 32)
+    ra, rs = oracle.logpsi(w.L, w.C, w.D, theta, sig)
+    re, rn = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[:1], nthreads=os.cpu_count() or 4)
+    return sig, theta, ra, rs, re, rn
+
+
+@pytest.mark.parametrize("prec,la_tol,e_tol", [("bf16", 0.25, BF16_SMALL_TOL), ("fp16", 0.05, FP16_TOL)])
+def test_tc_largest_lattice_L32(prec, la_tol, e_tol, l32_reference):
+    """L = 32 is the largest lattice of the tensor-core path; with C = 32
+    only the one-slab geometries fit shared memory.  log|psi| and sign
+    against the FP64 oracle: C N = 32768 log terms, 16 times those of the
+    L = 8 check, so the random rounding error is ~4 times larger (bounds
+    0.25 BF16, 0.05 FP16).  E_loc of one sample (~2000 neighbour
+    configurations; the plain FP32 path does not fit L = 32 with C = 32)
+    against the oracle, with the small-lattice tolerances."""
+    sig, theta, ra, rs, re, rn = l32_reference
+    w = inputs.Workload("t32", 32, 32, 6, prec, 6, kind="uniform", index=50 + 32)
+    v = make_ctx(w, theta=theta)
+    assert v.get_tiles(32)["slabs"] == 1
+    la, sg = v.logpsi(to_dev(sig))
+    np.testing.assert_array_equal(sg.cpu().numpy().astype(np.int32), rs)
+    assert np.abs(la.cpu().numpy() - ra).max() <= la_tol
+    e, nn = v.local_energy(to_dev(sig[:1]))
+    np.testing.assert_array_equal(nn.cpu().numpy(), rn)
+    assert (np.abs(e.cpu().numpy() - re) / (w.L * w.L)).max() <= e_tol
+    assert v.sync_status()[0] == VMC_OK
 
 
 @pytest.mark.parametrize("L", [6, 8, 16])
