@@ -531,7 +531,7 @@ struct Kern {
     // k / (C/8), i.e. plane g4 of cell m for C = 32, plane g4 & 1 of cell
     // 2 m + g4 / 2 for C = 16; one bias vector per thread.
     struct TileCtx {
-        int L, PW, RW, NRm, count, NQ;
+        int L, PW, RW, NRm, T, count, NQ;
         uint32_t mRW, mLP, PS;
         uint32_t out;           // output buffer (shared address)
         float bias[8];
@@ -540,7 +540,7 @@ struct Kern {
     __device__ __forceinline__ void load_tctx(int s, int l, int tid, TileCtx &k) const
     {
         const SlabMeta &m = c.slab[s];
-        k.L = m.L; k.PW = m.PW; k.RW = m.RW; k.NRm = m.NRm; k.count = m.count;
+        k.L = m.L; k.PW = m.PW; k.RW = m.RW; k.NRm = m.NRm; k.T = m.T; k.count = m.count;
         k.NQ = (m.L + 2) * m.PW;
         k.mRW = m.mRW; k.mLP = m.mLP; k.PS = m.PS;
         k.out = smem_u32(act_buf(s, l & 1));
@@ -558,10 +558,10 @@ struct Kern {
     // arithmetic interleaves.
     template <int M0, int N, bool POOL>
     __device__ __forceinline__ void put_chunks(const float (&v)[N][8], int g4, int r, int Y, int rX, int Yh,
-                                               const TileCtx &k, float *partF, int *partI)
+                                               bool fresh, const TileCtx &k, float *partF, int *partI)
     {
         const int L = k.L;
-        const bool row_in = (Y >= 1) & (Y <= L);
+        const bool row_in = (Y >= 1) & (Y <= L) & fresh;
         const int g = g4 & (CP8 - 1);
         // the lane's P cells are consecutive in X: configuration j and column x
         // of the first, then advance (wrapping into the next configuration)
@@ -631,11 +631,15 @@ struct Kern {
         const int rX = r - Y * k.RW;
         const int L = k.L;
         const int Yh = (Y == 1) ? L + 1 : ((Y == L) ? 0 : -1);
+        // the last tile starts early so as not to run past the grid: its
+        // first `ov` rows were already drained (and stored, bitwise the same)
+        // by the tile before; warps whose rows all lie there skip the work
+        const int ov = (t == k.T - 1) ? 128 * t - k.NRm : 0;
         float v[NM][8];
         if (ok) {
             tmem_ld_chunks<NM, 32>(ta, v);
             tmem_zero_chunks_async<NM, 32>(ta);
-            put_chunks<0, NM, POOL>(v, g4, r, Y, rX, Yh, k, partF, partI);
+            if (wq * 32 + 31 >= ov) put_chunks<0, NM, POOL>(v, g4, r, Y, rX, Yh, wq * 32 + lane >= ov, k, partF, partI);
             __syncwarp();
             tmem_wait_st();
         }
