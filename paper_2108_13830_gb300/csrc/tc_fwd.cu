@@ -453,23 +453,26 @@ struct Kern {
     {
         const int D = p.D, R = p.nslots;
         int issued[2] = {0, 0}, waited[2] = {0, 0};
-        auto issue_w = [&](long long step) {
+        // weight step `step` (buffer step & 1) holds layer l
+        auto issue_w = [&](long long step, int l) {
             const int bsel = (int)(step & 1);
-            const int l = (int)(step % (D + 1));
             const uint32_t bytes = (uint32_t)tc_layer_bytes(C, l);
             mbar_expect_tx(&c.w_full[bsel], bytes);
             bulk_g2s(smem + bsel * WB, p.wimg + tc_wimg_offset(C, l), bytes, &c.w_full[bsel]);
             issued[bsel]++;
         };
         if (mw == 0) {
-            issue_w(0);
-            issue_w(1);
+            issue_w(0, 0);
+            issue_w(1, D >= 1 ? 1 : 0);
         }
         bool dead[2] = {false, p.S < 2};
         int cnt[2] = {0, 0};
         uint32_t ph_ar[2] = {0, 0};
-        long long step = 0;           // weight step
-        long long n = 0;              // tile sequence number
+        long long step = 0;           // weight step; its layer is l (the loop runs every layer of every step)
+        // tile sequence number n, kept as its slot n % R, the slot's use
+        // parity (n / R) & 1 and its issuing warp n % NMMA
+        int nslot = 0, nwarp = 0;
+        uint32_t npar = 0;
         bool ok = true;
         while (ok && !(dead[0] && dead[1])) {
             for (int l = 0; l <= D && ok; ++l) {
@@ -491,10 +494,13 @@ struct Kern {
                         any = true;
                     }
                     const int T = *(volatile int *)&c.slab[s].T;
-                    for (int t = 0; t < T; ++t, ++n) {
-                        if ((int)(n % NMMA) != mw) continue;
-                        const int slot = (int)(n % R);
-                        const uint32_t use_par = (uint32_t)((n / R) & 1);
+                    for (int t = 0; t < T; ++t) {
+                        const int slot = nslot;
+                        const uint32_t use_par = npar;
+                        const bool mine = (nwarp == mw);
+                        if (++nslot == R) { nslot = 0; npar ^= 1u; }
+                        if (++nwarp == NMMA) nwarp = 0;
+                        if (!mine) continue;
                         if (!wait_bar(&c.t_empty[slot], use_par ^ 1u, 3)) { ok = false; break; }
                         tc_fence_after();
                         issue_tile(s, l, t, (int)(step & 1), tmem + (uint32_t)(slot * p.slotc));
@@ -505,7 +511,7 @@ struct Kern {
                 umma_commit(&c.w_empty[step & 1]);
                 if (step >= 1 && mw == 0) {
                     if (!wait_bar(&c.w_empty[(step - 1) & 1], (uint32_t)(((step - 1) >> 1) & 1), 4)) { ok = false; break; }
-                    issue_w(step + 1);
+                    issue_w(step + 1, l == D ? 0 : l + 1);
                 }
                 ++step;
             }
