@@ -373,7 +373,8 @@ def eloc_only(args, w, sig, theta, prec):
 
 def side_measurements(torch, VMC, ev, stream):
     """E_loc + O_k samples/s at L = 16 and L = 24 for the BF16 tensor-core and
-    the plain FP32 paths (FP32 on a sub-batch to bound the run time)."""
+    the plain FP32 paths (FP32 on a sub-batch to bound the run time), and
+    the transition rate of the batched Metropolis sampler."""
     out = {}
     for name, prec, B in (("L16_bf16", "bf16", 8192), ("L16_bf16", "fp32", 256),
                           ("L24_bf16_sr", "bf16", 4096), ("L24_bf16_sr", "fp32", 64)):
@@ -405,6 +406,33 @@ def side_measurements(torch, VMC, ev, stream):
                                  "eloc_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (te / 1e3) / 1e12}
         ctx.close()
         del O
+        torch.cuda.empty_cache()
+    # batched Metropolis transitions (vmc_metropolis): one forward per chain
+    # per transition, B chains advancing together
+    for name, B, steps in (("L16_bf16", 8192, 8), ("L24_bf16_sr", 4096, 8)):
+        w = inputs.WORKLOADS[name]
+        sig, theta = inputs.workload_inputs(w, batch=B)
+        u = torch.tensor(inputs.chain_uniforms(steps, B, inputs.rng_for(w.index, 11)), device="cuda")
+        ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, "bf16")
+        ctx.set_params(torch.tensor(theta, device="cuda"))
+        s = torch.tensor(sig, device="cuda")
+        la, _ = ctx.logpsi(s)
+        acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+        ctx.metropolis(s, la, u[:1], accepted=acc)
+        torch.cuda.synchronize()
+        acc.zero_()
+        a, b = ev(), ev()
+        a.record(stream)
+        ctx.metropolis(s, la, u, accepted=acc)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b)
+        out[f"mcmc_L{w.L}_bf16"] = {"transitions_per_s": B * steps / (t / 1e3), "chains": B, "steps": steps,
+                                    "ms": t, "acceptance": float(acc.sum().item()) / (B * steps),
+                                    "forward_tflops": B * steps * f_fwd(w.L, w.C, w.D) / (t / 1e3) / 1e12,
+                                    "sweep_ms": t * w.L * w.L / steps,
+                                    "launches": ctx.last_launch_count}
+        ctx.close()
         torch.cuda.empty_cache()
     return out
 

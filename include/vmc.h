@@ -126,6 +126,34 @@ int vmc_local_energy_ragged(vmc_ctx *ctx, const int8_t *packed_dev, const int64_
                             const int32_t *L_dev, int64_t B, int L_max,
                             double *eloc_dev, int32_t *n_nbr_dev, void *stream);
 
+/* Batched Metropolis sampling of |W(S)|^2 (Sec. 3.1, Fig. 2b-c; the chains
+ * of Sec. 3.2.1 advance together, their proposals forming one batch).  Each
+ * of B independent chains makes n_steps transitions.  Transition s of
+ * chain b:
+ *  - lists the J1 propose batch of sigma_b: the antiparallel pairs among the
+ *    bonds of every site i = y L + x to its right and to its lower neighbour
+ *    (periodic), in that order, site by site; n_b pairs;
+ *  - picks pair k = floor(u[s][b][0] n_b), clamped to 0..n_b - 1, and
+ *    exchanges its two spins into sigma';
+ *  - accepts sigma' when P >= u[s][b][1], with
+ *    P = exp(2 (log|psi(sigma')| - log|psi(sigma)|)) = (W(sigma') / W(sigma))^2,
+ *    times n_b / n'_b (the pair counts of sigma and sigma') when
+ *    hastings = 1.  The paper's rule is hastings = 0; its stationary law is
+ *    |psi|^2 n_b / Z, the corrected one |psi|^2 / Z.
+ *  - A chain with n_b = 0 has no move and stays.
+ * The log|psi| of the B proposals of a transition come from one batched
+ * forward (the arithmetic of vmc_logpsi), so a transition costs one forward
+ * per chain; the paper spaces recorded samples by L^2 transitions.
+ *  - sigma_dev int8 [B][L][L]: the chains, updated in place.
+ *  - logabs_dev double [B]: on entry log|psi(sigma_b)| as vmc_logpsi gives
+ *    it; on exit that of the final sigma_b (the accepted forward's value).
+ *  - u_dev double [n_steps][B][2]: the caller's uniform numbers in [0, 1).
+ *  - accepted_dev int32 [B] or NULL: incremented by each accepted move.
+ * B = 0 or n_steps = 0 is a no-op.  Workspace: about B (L^2 + 17) bytes, grown on
+ * the first call at a larger B. */
+int vmc_metropolis(vmc_ctx *ctx, int8_t *sigma_dev, double *logabs_dev, int64_t B,
+                   const double *u_dev, int n_steps, int hastings, int32_t *accepted_dev, void *stream);
+
 /* Per-sample log-derivatives O_bk = d log|psi(sigma_b)| / d theta_k (Eq. 5),
  * by a hand-written backward pass that recomputes the forward activations
  * (workspace bounded by the number of resident CTAs, not by B).

@@ -17,7 +17,7 @@ The chain follows Sec. 3.1 of arXiv:2108.13830 (Fig. 2b-c):
 
 Readings where the paper is silent:
  - Random numbers are inputs.  u[s, b, 0] selects pair k = floor(u n)
-   (clamped to n - 1) of the n pairs; u[s, b, 1] is r.
+   (clamped to 0 .. n - 1) of the n pairs; u[s, b, 1] is r.
  - P = exp(2 (log|psi(S')| - log|psi(S)|)) in FP64.
  - With hastings=True, P is multiplied by n(S) / n(S').  The proposal
    probability 1/n(S) is not symmetric, so without this factor the chain's
@@ -65,7 +65,7 @@ def propose(sigma, L, u0):
     for b in range(s.shape[0]):
         if n[b] == 0:
             continue
-        k = min(int(np.floor(u0[b] * n[b])), int(n[b]) - 1)
+        k = min(max(int(np.floor(u0[b] * n[b])), 0), int(n[b]) - 1)
         bond[b] = int(np.flatnonzero(flags[b])[k])
         i, j = bond_sites(L, bond[b])
         out[b, i], out[b, j] = s[b, j], s[b, i]

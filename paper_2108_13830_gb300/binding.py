@@ -51,6 +51,7 @@ _SIGS = {
     "vmc_local_energy": (_I, [_P, _P, _I64, _P, _P, _P]),
     "vmc_local_energy_ragged": (_I, [_P, _P, _P, _P, _I64, _I, _P, _P, _P]),
     "vmc_log_derivs": (_I, [_P, _P, _I64, _P, _I, _P]),
+    "vmc_metropolis": (_I, [_P, _P, _P, _I64, _P, _I, _I, _P, _P]),
     "vmc_sr_moments": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "vmc_sr_matvec": (_I, [_P, _P, _I64, _P, _P, _D, _P, _P]),
     "vmc_ot_vec": (_I, [_P, _P, _I64, _P, _P, _P]),
@@ -178,6 +179,24 @@ class VMC:
         self._check(lib().vmc_local_energy_ragged(self._h, _ptr(pk), _ptr(of), _ptr(Lt), B, int(L_max),
                                                   _ptr(e), _ptr(nn), _stream()))
         return e, nn
+
+    def metropolis(self, sigma, logabs, u, hastings=False, accepted=None):
+        """Advance the chains sigma [B, L, L] (int8, in place) and their
+        log|psi| (float64 [B], in place) by u.shape[0] transitions drawn
+        from u [steps, B, 2] (float64 in [0, 1)); accepted (int32 [B]) is
+        incremented by the accepted moves."""
+        if not (sigma.is_cuda and sigma.dtype == torch.int8 and sigma.is_contiguous()):
+            raise TypeError("sigma must be a contiguous CUDA int8 tensor (updated in place)")
+        if not (logabs.is_cuda and logabs.dtype == torch.float64 and logabs.is_contiguous()):
+            raise TypeError("logabs must be a contiguous CUDA float64 tensor (updated in place)")
+        uu = _dev(u, torch.float64, "u")
+        B = sigma.shape[0]
+        if uu.dim() != 3 or uu.shape[1] != B or uu.shape[2] != 2 or logabs.numel() != B:
+            raise ValueError("u must be [steps, B, 2] and logabs [B]")
+        if accepted is not None and not (accepted.is_cuda and accepted.dtype == torch.int32 and accepted.is_contiguous()):
+            raise TypeError("accepted must be a contiguous CUDA int32 tensor")
+        self._check(lib().vmc_metropolis(self._h, _ptr(sigma), _ptr(logabs), B, _ptr(uu), uu.shape[0],
+                                         int(bool(hastings)), _ptr(accepted), _stream()))
 
     def log_derivs(self, sigma, dtype=torch.float32, out=None):
         s = _dev(sigma, torch.int8, "sigma")

@@ -107,7 +107,7 @@ void vmc_destroy(vmc_ctx *ctx)
     cudaFree(ctx->theta64); cudaFree(ctx->theta32); cudaFree(ctx->wsimt); cudaFree(ctx->wsimtT);
     cudaFree(ctx->bias); cudaFree(ctx->bias32); cudaFree(ctx->wimg);
     cudaFree(ctx->status); cudaFree(ctx->counter);
-    cudaFree(ctx->ws); cudaFree(ctx->sr_ws);
+    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws);
     delete ctx;
 }
 
@@ -181,6 +181,19 @@ int vmc_local_energy_ragged(vmc_ctx *ctx, const int8_t *packed_dev, const int64_
     if (vmc_is_tc(ctx->arch.precision))
         return vmc_tc_eloc(ctx, 1, packed_dev, offs_dev, L_dev, B, L_max, eloc_dev, nullptr, n_nbr_dev, (cudaStream_t)stream);
     return vmc_simt_eloc(ctx, 1, packed_dev, offs_dev, L_dev, B, L_max, eloc_dev, nullptr, n_nbr_dev, (cudaStream_t)stream);
+}
+
+int vmc_metropolis(vmc_ctx *ctx, int8_t *sigma_dev, double *logabs_dev, int64_t B, const double *u_dev,
+                   int n_steps, int hastings, int32_t *accepted_dev, void *stream)
+{
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (B < 0 || n_steps < 0) return vmc_fail(ctx, VMC_ERR_ARG, "negative batch or step count");
+    if (hastings != 0 && hastings != 1) return vmc_fail(ctx, VMC_ERR_ARG, "hastings must be 0 or 1");
+    if (B == 0 || n_steps == 0) return VMC_OK;
+    if (!sigma_dev || !logabs_dev || !u_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
+    return vmc_metropolis_impl(ctx, sigma_dev, logabs_dev, B, u_dev, n_steps, hastings, accepted_dev,
+                               (cudaStream_t)stream);
 }
 
 int vmc_log_derivs(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B, void *O_dev, int dtype, void *stream)

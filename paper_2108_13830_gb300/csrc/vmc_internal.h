@@ -65,6 +65,8 @@ struct vmc_ctx {
     size_t ws_bytes = 0;
     void *sr_ws = nullptr;
     size_t sr_ws_bytes = 0;
+    void *mc_ws = nullptr;       // Metropolis proposals and their log|psi|
+    size_t mc_ws_bytes = 0;
 
     int64_t wait_budget_ns = 2000000000LL;
     std::map<int, TileChoice> tiles;
@@ -104,6 +106,10 @@ int vmc_tc_eloc(vmc_ctx *ctx, int mode, const int8_t *sigma, const int64_t *offs
                 int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr, cudaStream_t s);
 int vmc_tc_default_tiles(const vmc_ctx *ctx, int L, TileChoice *t);
 int vmc_tc_debug_timeout(vmc_ctx *ctx, int64_t budget_ns, cudaStream_t s);
+
+// Metropolis sampling (mcmc.cu)
+int vmc_metropolis_impl(vmc_ctx *ctx, int8_t *sigma, double *logabs, int64_t B, const double *u, int n_steps,
+                        int hastings, int32_t *accepted, cudaStream_t s);
 
 // SR (sr.cu)
 int vmc_sr_moments_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m,

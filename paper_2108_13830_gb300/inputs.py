@@ -189,3 +189,9 @@ def synthetic_O(m: int, n: int, rng: np.random.Generator, dtype=np.float32) -> n
 def synthetic_E(m: int, rng: np.random.Generator) -> np.ndarray:
     """Stand-in local energies around -0.5 per site of a 10x10 lattice."""
     return -50.0 + 3.0 * rng.standard_normal(m)
+
+
+def chain_uniforms(steps: int, B: int, rng: np.random.Generator) -> np.ndarray:
+    """Random numbers of `steps` Metropolis transitions of B chains:
+    float64 [steps, B, 2] in [0, 1) (pair selector, acceptance threshold)."""
+    return rng.random((steps, B, 2))
