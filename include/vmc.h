@@ -215,6 +215,15 @@ int vmc_ot_vec_noalloc(const float *O_dev, int64_t m, int64_t n, const double *w
 int vmc_sr_solve(vmc_ctx *ctx, const float *O_dev, const double *eloc_dev, int64_t m,
                  double shift, int iters, double *x_dev, double *resid_out, void *stream);
 
+/* The SR parameter update of Eq. 6, theta <- theta - eta x, on the
+ * context's FP64 parameter vector, with x the direction vmc_sr_solve
+ * returns (Delta = eta x, x = (S + shift I)^{-1} G).  Each entry is
+ * theta_k - (eta x_k), the product and the difference rounded separately
+ * in FP64.  The working images of the context's precision are re-derived
+ * from the updated vector, so the next forward uses it.  x_dev double [n]
+ * (device).  Requires parameters to be set. */
+int vmc_sr_update(vmc_ctx *ctx, const double *x_dev, double eta, void *stream);
+
 /* Synchronise `stream` and read (then clear) the device status word:
  * VMC_OK, VMC_ERR_NONFINITE (with *nonfinite = number of samples, if
  * non-NULL), VMC_ERR_TIMEOUT or VMC_ERR_ARG. */

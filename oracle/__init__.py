@@ -150,3 +150,8 @@ def sr_cg(O, E, shift, iters):
     x = _np.zeros(n)
     res = lib().orc_sr_cg(O, m, n, ob, g, float(shift), int(iters), x)
     return x, float(res)
+
+
+def sr_update(theta, x, eta):
+    """theta - eta x: the parameter step of Eq. 6 (Delta = eta x)."""
+    return _f64(theta) - float(eta) * _f64(x)

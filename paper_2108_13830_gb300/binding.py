@@ -57,6 +57,7 @@ _SIGS = {
     "vmc_ot_vec": (_I, [_P, _P, _I64, _P, _P, _P]),
     "vmc_ot_vec_noalloc": (_I, [_P, _I64, _I64, _P, _P, _P]),
     "vmc_sr_solve": (_I, [_P, _P, _P, _I64, _D, _I, _P, ct.POINTER(_D), _P]),
+    "vmc_sr_update": (_I, [_P, _P, _D, _P]),
     "vmc_sync_status": (_I, [_P, _P, ct.POINTER(_I64)]),
     "vmc_set_wait_budget": (_I, [_P, _I64]),
     "vmc_debug_wait_timeout": (_I, [_P, _I64, _P]),
@@ -239,6 +240,13 @@ class VMC:
         self._check(lib().vmc_sr_solve(self._h, _ptr(O), _ptr(E), O.shape[0], float(shift), int(iters),
                                        _ptr(x), ct.byref(r) if resid else None, _stream()))
         return x, (r.value if resid else None)
+
+    def sr_update(self, x, eta):
+        """theta <- theta - eta x on the context's parameters (Eq. 6)."""
+        x = _dev(x, torch.float64, "x")
+        if x.numel() != self.n:
+            raise ValueError(f"x has {x.numel()} values, expected {self.n}")
+        self._check(lib().vmc_sr_update(self._h, _ptr(x), float(eta), _stream()))
 
     def sync_status(self):
         """(code, nonfinite count) after synchronising the current stream."""

@@ -20,6 +20,18 @@ __global__ void cvt_theta_kernel(const Tin *__restrict__ in, double *t64, float 
     }
 }
 
+// The SR update of Eq. 6 on the master copy: theta <- theta - eta x, one
+// product and one difference, each rounded (no fused multiply-add), so
+// that the result is the plain FP64 expression.
+__global__ void theta_step_kernel(double *t64, float *t32, const double *__restrict__ x, double eta, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = __dsub_rn(t64[i], __dmul_rn(eta, x[i]));
+        t64[i] = v;
+        t32[i] = (float)v;
+    }
+}
+
 // SIMT images.  Forward: out[l][cb][ci][t][co'] = W_l[cb*CO+co'][ci][t].
 // Transposed (l >= 1): out[l][cb][co][t][ci'] = W_l[co][cb*CO+ci'][8 - t].
 template <typename T>
@@ -103,6 +115,14 @@ int vmc_prepare_params(vmc_ctx *ctx, const void *theta, int dtype, cudaStream_t 
         vmc::cvt_theta_kernel<double><<<grid, blk, 0, s>>>(static_cast<const double *>(theta), ctx->theta64, ctx->theta32, n);
     else
         vmc::cvt_theta_kernel<float><<<grid, blk, 0, s>>>(static_cast<const float *>(theta), ctx->theta64, ctx->theta32, n);
+    ctx->launches += 1;
+    return vmc_derive_images(ctx, s);
+}
+
+int vmc_derive_images(vmc_ctx *ctx, cudaStream_t s)
+{
+    const int C = ctx->arch.channels, D = ctx->arch.n_layers_cc;
+    const int grid = 2 * ctx->sm_count, blk = 256;
     const int CO = vmc::simt_co(C);
     if (ctx->arch.precision == VMC_FP64)
         vmc::simt_image_kernel<double><<<grid, blk, 0, s>>>(ctx->theta64, (double *)ctx->wsimt, (double *)ctx->wsimtT,
@@ -110,11 +130,19 @@ int vmc_prepare_params(vmc_ctx *ctx, const void *theta, int dtype, cudaStream_t 
     else
         vmc::simt_image_kernel<float><<<grid, blk, 0, s>>>(ctx->theta64, (float *)ctx->wsimt, (float *)ctx->wsimtT,
                                                            (float *)ctx->bias, C, D, CO);
-    ctx->launches += 2;
+    ctx->launches += 1;
     if (vmc_is_tc(ctx->arch.precision)) {
         vmc::tc_image_kernel<<<grid, blk, 0, s>>>(ctx->theta64, ctx->wimg, ctx->bias32, C, D,
                                                   ctx->arch.precision == VMC_FP16);
         ctx->launches += 1;
     }
     return vmc_cuda_check(ctx, cudaGetLastError(), "prepare params");
+}
+
+int vmc_sr_update_impl(vmc_ctx *ctx, const double *x, double eta, cudaStream_t s)
+{
+    vmc::theta_step_kernel<<<2 * ctx->sm_count, 256, 0, s>>>(ctx->theta64, ctx->theta32, x, eta, ctx->n);
+    ctx->launches += 1;
+    const int rc = vmc_cuda_check(ctx, cudaGetLastError(), "theta step");
+    return rc ? rc : vmc_derive_images(ctx, s);
 }

@@ -1,5 +1,6 @@
 // C ABI of libvmc (declared in include/vmc.h): argument checking, context
 // lifetime, workspace management and dispatch to the kernels.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -246,6 +247,15 @@ int vmc_sr_solve(vmc_ctx *ctx, const float *O_dev, const double *eloc_dev, int64
     if (!(shift >= 0.0)) return vmc_fail(ctx, VMC_ERR_ARG, "shift must be >= 0");
     if (!O_dev || !eloc_dev || !x_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
     return vmc_sr_solve_impl(ctx, O_dev, eloc_dev, m, shift, iters, x_dev, resid_out, (cudaStream_t)stream);
+}
+
+int vmc_sr_update(vmc_ctx *ctx, const double *x_dev, double eta, void *stream)
+{
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (!x_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
+    if (!std::isfinite(eta)) return vmc_fail(ctx, VMC_ERR_ARG, "eta must be finite");
+    return vmc_sr_update_impl(ctx, x_dev, eta, (cudaStream_t)stream);
 }
 
 int vmc_sync_status(vmc_ctx *ctx, void *stream, int64_t *nonfinite)

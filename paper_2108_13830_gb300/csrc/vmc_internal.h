@@ -92,6 +92,8 @@ int vmc_ensure_ws(vmc_ctx *ctx, void **buf, size_t *cur, size_t need);
 
 // parameter preparation (prep.cu)
 int vmc_prepare_params(vmc_ctx *ctx, const void *theta, int dtype, cudaStream_t s);
+int vmc_derive_images(vmc_ctx *ctx, cudaStream_t s);           // per-precision images from theta64
+int vmc_sr_update_impl(vmc_ctx *ctx, const double *x, double eta, cudaStream_t s);
 
 // SIMT forward / local energy (simt_fwd.cu)
 int vmc_simt_eloc(vmc_ctx *ctx, int mode, const int8_t *sigma, const int64_t *offs, const int32_t *Ls,
