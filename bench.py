@@ -407,6 +407,55 @@ def side_measurements(torch, VMC, ev, stream):
         ctx.close()
         del O
         torch.cuda.empty_cache()
+    # ragged mixed-L batch (L = 8, 10, 12, 16 interleaved, 2048 each, C = 16,
+    # D = 6, FP16): one persistent launch, replayed from a CUDA graph,
+    # against the same samples split into one launch per lattice size
+    w = inputs.WORKLOADS["ragged_8_16"]
+    packed, offs, Ls, theta = inputs.ragged_inputs(w)
+    ctx = VMC(max(w.Ls), w.J1, w.J2, w.C, w.D, w.precision)
+    ctx.set_params(torch.tensor(theta, device="cuda"))
+    pk, of, Lt = (torch.tensor(x, device="cuda") for x in (packed, offs, Ls))
+    B = len(offs)
+    e, nn = ctx.local_energy_ragged(pk, of, Lt, max(w.Ls))
+    flops = float(sum((1.0 + float(k)) * f_fwd(int(L), w.C, w.D) for k, L in zip(nn.cpu().numpy(), Ls)))
+    e2 = torch.empty_like(e)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ctx.local_energy_ragged(pk, of, Lt, max(w.Ls), out=e2, n_nbr=False)
+    g.replay()
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record(stream)
+    g.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_r = a.elapsed_time(b)
+    per_L = {}
+    t_split = 0.0
+    for L in w.Ls:
+        idx = np.flatnonzero(Ls == L)
+        sig = np.stack([packed[offs[i]:offs[i] + L * L] for i in idx]).reshape(-1, L, L)
+        cl = VMC(int(L), w.J1, w.J2, w.C, w.D, w.precision)
+        cl.set_params(torch.tensor(theta, device="cuda"))
+        sL = torch.tensor(sig, device="cuda")
+        eL = torch.empty(len(idx), dtype=torch.float64, device="cuda")
+        cl.local_energy(sL, out=eL, n_nbr=False)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        cl.local_energy(sL, out=eL, n_nbr=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        tL = a.elapsed_time(b)
+        t_split += tL
+        fl = float(sum((1.0 + float(k)) for k in nn.cpu().numpy()[idx])) * f_fwd(int(L), w.C, w.D)
+        per_L[str(int(L))] = {"samples": int(len(idx)), "ms": tL, "tflops": fl / (tL / 1e3) / 1e12}
+        cl.close()
+    out["ragged_8_16_fp16"] = {"samples": B, "ms": t_r, "samples_per_s": B / (t_r / 1e3),
+                               "eloc_tflops": flops / (t_r / 1e3) / 1e12, "launch": "one persistent launch, CUDA graph",
+                               "per_L_separate_launches": per_L, "separate_total_ms": t_split}
+    ctx.close()
+    torch.cuda.empty_cache()
     # batched Metropolis transitions (vmc_metropolis): one forward per chain
     # per transition, B chains advancing together
     for name, B, steps in (("L16_bf16", 8192, 8), ("L24_bf16_sr", 4096, 8)):
