@@ -456,6 +456,27 @@ def side_measurements(torch, VMC, ev, stream):
                                "per_L_separate_launches": per_L, "separate_total_ms": t_split}
     ctx.close()
     torch.cuda.empty_cache()
+    # rotationally symmetrised local energy (vmc_local_energy_sym): four
+    # forwards per configuration, 512 samples (two workspace chunks at L = 24)
+    w = inputs.WORKLOADS["L24_bf16_sr"]
+    sig, theta = inputs.workload_inputs(w, batch=512)
+    ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, "bf16")
+    ctx.set_params(torch.tensor(theta, device="cuda"))
+    s = torch.tensor(sig, device="cuda")
+    _, nn = ctx.local_energy_sym(s)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record(stream)
+    ctx.local_energy_sym(s, n_nbr=False)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b)
+    ncfg = 4 * int(512 + nn.sum().item())
+    out["eloc_sym_L24_bf16"] = {"samples": 512, "ms": t, "samples_per_s": 512 / (t / 1e3),
+                                "forward_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (t / 1e3) / 1e12,
+                                "launches": ctx.last_launch_count}
+    ctx.close()
+    torch.cuda.empty_cache()
     # batched Metropolis transitions (vmc_metropolis): one forward per chain
     # per transition, B chains advancing together
     for name, B, steps in (("L16_bf16", 8192, 8), ("L24_bf16_sr", 4096, 8)):

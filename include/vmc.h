@@ -126,6 +126,32 @@ int vmc_local_energy_ragged(vmc_ctx *ctx, const int8_t *packed_dev, const int64_
                             const int32_t *L_dev, int64_t B, int L_max,
                             double *eloc_dev, int32_t *n_nbr_dev, void *stream);
 
+/* Rotationally symmetrised amplitude (Sec. 2.2, the equation after Eq. 9;
+ * Sec. 3.4 applies it in the last fine-tuning stage):
+ *     W~(S) = sum_{i=0..3} W(T^i S),  W = (-1)^{M_A} W_CNN,
+ * T the 90-degree rotation of the L x L lattice.  Each W~ evaluates the
+ * context's forward (the arithmetic of vmc_logpsi, signs included) on the
+ * four rotations, i.e. four times the work, and sums the signed amplitudes
+ * in FP64 after factoring out the largest.  The rotated configurations are
+ * materialised in device memory, a chunk of samples at a time (workspace
+ * up to about 1 GiB).
+ *  - vmc_logpsi_sym: log|W~| and sgn W~, layouts as vmc_logpsi.
+ *  - vmc_local_energy_sym: E_loc of Eq. 4-5 with W~ for sigma and for every
+ *    exchange neighbour (the bonds of vmc_local_energy, full signs);
+ *    n_nbr_dev as there.  Synchronises `stream` once, to size the chunks
+ *    from the neighbour counts.
+ *  - vmc_log_derivs_sym: O_bk = d log|W~| / d theta_k
+ *    = sum_i (W(T^i sigma_b) / W~(sigma_b)) O_k(T^i sigma_b); O_dev and
+ *    dtype as vmc_log_derivs.
+ * A sample with W~ = 0 or a non-finite result gets NaN (E_loc) or -inf
+ * (log|W~|) and raises VMC_ERR_NONFINITE in vmc_sync_status (E_loc). */
+int vmc_logpsi_sym(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B,
+                   double *logabs_dev, int8_t *sign_dev, void *stream);
+int vmc_local_energy_sym(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B,
+                         double *eloc_dev, int32_t *n_nbr_dev, void *stream);
+int vmc_log_derivs_sym(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B,
+                       void *O_dev, int dtype, void *stream);
+
 /* Batched Metropolis sampling of |W(S)|^2 (Sec. 3.1, Fig. 2b-c; the chains
  * of Sec. 3.2.1 advance together, their proposals forming one batch).  Each
  * of B independent chains makes n_steps transitions.  Transition s of

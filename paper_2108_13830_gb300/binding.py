@@ -52,6 +52,9 @@ _SIGS = {
     "vmc_local_energy_ragged": (_I, [_P, _P, _P, _P, _I64, _I, _P, _P, _P]),
     "vmc_log_derivs": (_I, [_P, _P, _I64, _P, _I, _P]),
     "vmc_metropolis": (_I, [_P, _P, _P, _I64, _P, _I, _I, _P, _P]),
+    "vmc_logpsi_sym": (_I, [_P, _P, _I64, _P, _P, _P]),
+    "vmc_local_energy_sym": (_I, [_P, _P, _I64, _P, _P, _P]),
+    "vmc_log_derivs_sym": (_I, [_P, _P, _I64, _P, _I, _P]),
     "vmc_sr_moments": (_I, [_P, _P, _P, _I64, _P, _P, _P, _P]),
     "vmc_sr_matvec": (_I, [_P, _P, _I64, _P, _P, _D, _P, _P]),
     "vmc_ot_vec": (_I, [_P, _P, _I64, _P, _P, _P]),
@@ -180,6 +183,31 @@ class VMC:
         self._check(lib().vmc_local_energy_ragged(self._h, _ptr(pk), _ptr(of), _ptr(Lt), B, int(L_max),
                                                   _ptr(e), _ptr(nn), _stream()))
         return e, nn
+
+    def logpsi_sym(self, sigma):
+        """(log|W~|, sgn W~) of the rotationally symmetrised amplitude."""
+        s = _dev(sigma, torch.int8, "sigma")
+        B = s.shape[0]
+        la = torch.empty(B, dtype=torch.float64, device=s.device)
+        sg = torch.empty(B, dtype=torch.int8, device=s.device)
+        self._check(lib().vmc_logpsi_sym(self._h, _ptr(s), B, _ptr(la), _ptr(sg), _stream()))
+        return la, sg
+
+    def local_energy_sym(self, sigma, n_nbr=True):
+        s = _dev(sigma, torch.int8, "sigma")
+        B = s.shape[0]
+        e = torch.empty(B, dtype=torch.float64, device=s.device)
+        nn = torch.empty(B, dtype=torch.int32, device=s.device) if n_nbr else None
+        self._check(lib().vmc_local_energy_sym(self._h, _ptr(s), B, _ptr(e), _ptr(nn), _stream()))
+        return e, nn
+
+    def log_derivs_sym(self, sigma, dtype=torch.float32):
+        s = _dev(sigma, torch.int8, "sigma")
+        B = s.shape[0]
+        O = torch.empty(B, self.n, dtype=dtype, device=s.device)
+        code = VMC_FP64 if O.dtype == torch.float64 else VMC_FP32
+        self._check(lib().vmc_log_derivs_sym(self._h, _ptr(s), B, _ptr(O), code, _stream()))
+        return O
 
     def metropolis(self, sigma, logabs, u, hastings=False, accepted=None):
         """Advance the chains sigma [B, L, L] (int8, in place) and their

@@ -108,7 +108,7 @@ void vmc_destroy(vmc_ctx *ctx)
     cudaFree(ctx->theta64); cudaFree(ctx->theta32); cudaFree(ctx->wsimt); cudaFree(ctx->wsimtT);
     cudaFree(ctx->bias); cudaFree(ctx->bias32); cudaFree(ctx->wimg);
     cudaFree(ctx->status); cudaFree(ctx->counter);
-    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws);
+    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws); cudaFree(ctx->sym_ws); cudaFree(ctx->sym_cnt);
     delete ctx;
 }
 
@@ -182,6 +182,40 @@ int vmc_local_energy_ragged(vmc_ctx *ctx, const int8_t *packed_dev, const int64_
     if (vmc_is_tc(ctx->arch.precision))
         return vmc_tc_eloc(ctx, 1, packed_dev, offs_dev, L_dev, B, L_max, eloc_dev, nullptr, n_nbr_dev, (cudaStream_t)stream);
     return vmc_simt_eloc(ctx, 1, packed_dev, offs_dev, L_dev, B, L_max, eloc_dev, nullptr, n_nbr_dev, (cudaStream_t)stream);
+}
+
+int vmc_logpsi_sym(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B, double *logabs_dev, int8_t *sign_dev, void *stream)
+{
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (B < 0) return vmc_fail(ctx, VMC_ERR_ARG, "negative batch");
+    if (B == 0) return VMC_OK;
+    if (!sigma_dev || !logabs_dev || !sign_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
+    return vmc_logpsi_sym_impl(ctx, sigma_dev, B, logabs_dev, sign_dev, (cudaStream_t)stream);
+}
+
+int vmc_local_energy_sym(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B, double *eloc_dev, int32_t *n_nbr_dev,
+                         void *stream)
+{
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (B < 0) return vmc_fail(ctx, VMC_ERR_ARG, "negative batch");
+    if (B == 0) return VMC_OK;
+    if (!sigma_dev || !eloc_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
+    return vmc_local_energy_sym_impl(ctx, sigma_dev, B, eloc_dev, n_nbr_dev, (cudaStream_t)stream);
+}
+
+int vmc_log_derivs_sym(vmc_ctx *ctx, const int8_t *sigma_dev, int64_t B, void *O_dev, int dtype, void *stream)
+{
+    int rc = check_ready(ctx);
+    if (rc) return rc;
+    if (B < 0) return vmc_fail(ctx, VMC_ERR_ARG, "negative batch");
+    if (B == 0) return VMC_OK;
+    if (!sigma_dev || !O_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
+    if (dtype != VMC_FP32 && dtype != VMC_FP64) return vmc_fail(ctx, VMC_ERR_ARG, "O dtype must be FP32 or FP64");
+    if (dtype == VMC_FP64 && ctx->arch.precision != VMC_FP64)
+        return vmc_fail(ctx, VMC_ERR_ARG, "FP64 O output needs an FP64 context");
+    return vmc_log_derivs_sym_impl(ctx, sigma_dev, B, O_dev, dtype, (cudaStream_t)stream);
 }
 
 int vmc_metropolis(vmc_ctx *ctx, int8_t *sigma_dev, double *logabs_dev, int64_t B, const double *u_dev,

@@ -67,6 +67,10 @@ struct vmc_ctx {
     size_t sr_ws_bytes = 0;
     void *mc_ws = nullptr;       // Metropolis proposals and their log|psi|
     size_t mc_ws_bytes = 0;
+    void *sym_ws = nullptr;      // rotated configurations, their log|psi| and O rows
+    size_t sym_ws_bytes = 0;
+    void *sym_cnt = nullptr;     // per-sample neighbour counts, diagonals, offsets
+    size_t sym_cnt_bytes = 0;
 
     int64_t wait_budget_ns = 2000000000LL;
     std::map<int, TileChoice> tiles;
@@ -112,6 +116,12 @@ int vmc_tc_debug_timeout(vmc_ctx *ctx, int64_t budget_ns, cudaStream_t s);
 // Metropolis sampling (mcmc.cu)
 int vmc_metropolis_impl(vmc_ctx *ctx, int8_t *sigma, double *logabs, int64_t B, const double *u, int n_steps,
                         int hastings, int32_t *accepted, cudaStream_t s);
+
+// rotationally symmetrised amplitude (sym.cu)
+int vmc_logpsi_sym_impl(vmc_ctx *ctx, const int8_t *sigma, int64_t B, double *logabs, int8_t *sign, cudaStream_t s);
+int vmc_local_energy_sym_impl(vmc_ctx *ctx, const int8_t *sigma, int64_t B, double *eloc, int32_t *n_nbr,
+                              cudaStream_t s);
+int vmc_log_derivs_sym_impl(vmc_ctx *ctx, const int8_t *sigma, int64_t B, void *O, int dtype, cudaStream_t s);
 
 // SR (sr.cu)
 int vmc_sr_moments_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m,
