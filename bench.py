@@ -207,6 +207,8 @@ def main():
                     help="profiling case: only the local-energy launch, no JSON contract line")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
     ap.add_argument("--precision", default="", help="override the tensor-core operand type (bf16 | fp16)")
+    ap.add_argument("--side", default="", choices=("",) + SIDE_PARTS,
+                    help="profiling case: one side measurement only, printed as JSON, no contract line")
     args = ap.parse_args()
     w = inputs.WORKLOADS[args.workload]
     if args.batch:
@@ -235,6 +237,10 @@ def main():
     prec = args.precision or ("bf16" if w.precision in ("bf16", "fp32") else w.precision)
     if args.eloc_only:
         return eloc_only(args, w, sig, theta, prec)
+    if args.side:
+        ev0 = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+        print(json.dumps(side_measurements(torch, VMC, ev0, torch.cuda.current_stream(), parts=(args.side,))))
+        return 0
     ctx = VMC(L, w.J1, w.J2, C, D, prec)
     ctx.set_params(torch.tensor(theta, device="cuda"))
     s_dev = torch.tensor(sig, device="cuda")
@@ -371,139 +377,146 @@ def eloc_only(args, w, sig, theta, prec):
     return 0 if rc == 0 else 1
 
 
-def side_measurements(torch, VMC, ev, stream):
+SIDE_PARTS = ("eloc", "ragged", "sym", "mcmc")
+
+
+def side_measurements(torch, VMC, ev, stream, parts=SIDE_PARTS):
     """E_loc + O_k samples/s at L = 16 and L = 24 for the BF16 tensor-core and
     the plain FP32 paths (FP32 on a sub-batch to bound the run time), and
     the transition rate of the batched Metropolis sampler."""
     out = {}
-    for name, prec, B in (("L16_bf16", "bf16", 8192), ("L16_bf16", "fp32", 256),
-                          ("L24_bf16_sr", "bf16", 4096), ("L24_bf16_sr", "fp32", 64)):
-        w = inputs.WORKLOADS[name]
-        sig, theta = inputs.workload_inputs(w, batch=B)
-        ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, prec)
-        ctx.set_params(torch.tensor(theta, device="cuda"))
-        s = torch.tensor(sig, device="cuda")
-        e = torch.empty(B, dtype=torch.float64, device="cuda")
-        O = torch.empty(B, ctx.n, dtype=torch.float32, device="cuda")
-        _, nn = ctx.local_energy(s)
-        ncfg = int(B + nn.sum().item())
-        ctx.log_derivs(s, out=O)
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(2):
-            a, b, c = ev(), ev(), ev()
-            a.record(stream)
-            ctx.local_energy(s, out=e, n_nbr=False)
-            b.record(stream)
+    if "eloc" in parts:
+        for name, prec, B in (("L16_bf16", "bf16", 8192), ("L16_bf16", "fp32", 256),
+                              ("L24_bf16_sr", "bf16", 4096), ("L24_bf16_sr", "fp32", 64)):
+            w = inputs.WORKLOADS[name]
+            sig, theta = inputs.workload_inputs(w, batch=B)
+            ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, prec)
+            ctx.set_params(torch.tensor(theta, device="cuda"))
+            s = torch.tensor(sig, device="cuda")
+            e = torch.empty(B, dtype=torch.float64, device="cuda")
+            O = torch.empty(B, ctx.n, dtype=torch.float32, device="cuda")
+            _, nn = ctx.local_energy(s)
+            ncfg = int(B + nn.sum().item())
             ctx.log_derivs(s, out=O)
-            c.record(stream)
             torch.cuda.synchronize()
-            ts.append((a.elapsed_time(b), b.elapsed_time(c)))
-        te = min(t[0] for t in ts)
-        to = min(t[1] for t in ts)
-        out[f"L{w.L}_{prec}"] = {"samples_per_s": B / ((te + to) / 1e3), "batch": B,
-                                 "eloc_ms": te, "log_derivs_ms": to,
-                                 "eloc_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (te / 1e3) / 1e12}
-        ctx.close()
-        del O
-        torch.cuda.empty_cache()
-    # ragged mixed-L batch (L = 8, 10, 12, 16 interleaved, 2048 each, C = 16,
-    # D = 6, FP16): one persistent launch, replayed from a CUDA graph,
-    # against the same samples split into one launch per lattice size
-    w = inputs.WORKLOADS["ragged_8_16"]
-    packed, offs, Ls, theta = inputs.ragged_inputs(w)
-    ctx = VMC(max(w.Ls), w.J1, w.J2, w.C, w.D, w.precision)
-    ctx.set_params(torch.tensor(theta, device="cuda"))
-    pk, of, Lt = (torch.tensor(x, device="cuda") for x in (packed, offs, Ls))
-    B = len(offs)
-    e, nn = ctx.local_energy_ragged(pk, of, Lt, max(w.Ls))
-    flops = float(sum((1.0 + float(k)) * f_fwd(int(L), w.C, w.D) for k, L in zip(nn.cpu().numpy(), Ls)))
-    e2 = torch.empty_like(e)
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        ctx.local_energy_ragged(pk, of, Lt, max(w.Ls), out=e2, n_nbr=False)
-    g.replay()
-    torch.cuda.synchronize()
-    a, b = ev(), ev()
-    a.record(stream)
-    g.replay()
-    b.record(stream)
-    torch.cuda.synchronize()
-    t_r = a.elapsed_time(b)
-    per_L = {}
-    t_split = 0.0
-    for L in w.Ls:
-        idx = np.flatnonzero(Ls == L)
-        sig = np.stack([packed[offs[i]:offs[i] + L * L] for i in idx]).reshape(-1, L, L)
-        cl = VMC(int(L), w.J1, w.J2, w.C, w.D, w.precision)
-        cl.set_params(torch.tensor(theta, device="cuda"))
-        sL = torch.tensor(sig, device="cuda")
-        eL = torch.empty(len(idx), dtype=torch.float64, device="cuda")
-        cl.local_energy(sL, out=eL, n_nbr=False)
+            ts = []
+            for _ in range(2):
+                a, b, c = ev(), ev(), ev()
+                a.record(stream)
+                ctx.local_energy(s, out=e, n_nbr=False)
+                b.record(stream)
+                ctx.log_derivs(s, out=O)
+                c.record(stream)
+                torch.cuda.synchronize()
+                ts.append((a.elapsed_time(b), b.elapsed_time(c)))
+            te = min(t[0] for t in ts)
+            to = min(t[1] for t in ts)
+            out[f"L{w.L}_{prec}"] = {"samples_per_s": B / ((te + to) / 1e3), "batch": B,
+                                     "eloc_ms": te, "log_derivs_ms": to,
+                                     "eloc_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (te / 1e3) / 1e12}
+            ctx.close()
+            del O
+            torch.cuda.empty_cache()
+    if "ragged" in parts:
+        # ragged mixed-L batch (L = 8, 10, 12, 16 interleaved, 2048 each, C = 16,
+        # D = 6, FP16): one persistent launch, replayed from a CUDA graph,
+        # against the same samples split into one launch per lattice size
+        w = inputs.WORKLOADS["ragged_8_16"]
+        packed, offs, Ls, theta = inputs.ragged_inputs(w)
+        ctx = VMC(max(w.Ls), w.J1, w.J2, w.C, w.D, w.precision)
+        ctx.set_params(torch.tensor(theta, device="cuda"))
+        pk, of, Lt = (torch.tensor(x, device="cuda") for x in (packed, offs, Ls))
+        B = len(offs)
+        e, nn = ctx.local_energy_ragged(pk, of, Lt, max(w.Ls))
+        flops = float(sum((1.0 + float(k)) * f_fwd(int(L), w.C, w.D) for k, L in zip(nn.cpu().numpy(), Ls)))
+        e2 = torch.empty_like(e)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ctx.local_energy_ragged(pk, of, Lt, max(w.Ls), out=e2, n_nbr=False)
+        g.replay()
         torch.cuda.synchronize()
         a, b = ev(), ev()
         a.record(stream)
-        cl.local_energy(sL, out=eL, n_nbr=False)
+        g.replay()
         b.record(stream)
         torch.cuda.synchronize()
-        tL = a.elapsed_time(b)
-        t_split += tL
-        fl = float(sum((1.0 + float(k)) for k in nn.cpu().numpy()[idx])) * f_fwd(int(L), w.C, w.D)
-        per_L[str(int(L))] = {"samples": int(len(idx)), "ms": tL, "tflops": fl / (tL / 1e3) / 1e12}
-        cl.close()
-    out["ragged_8_16_fp16"] = {"samples": B, "ms": t_r, "samples_per_s": B / (t_r / 1e3),
-                               "eloc_tflops": flops / (t_r / 1e3) / 1e12, "launch": "one persistent launch, CUDA graph",
-                               "per_L_separate_launches": per_L, "separate_total_ms": t_split}
-    ctx.close()
-    torch.cuda.empty_cache()
-    # rotationally symmetrised local energy (vmc_local_energy_sym): four
-    # forwards per configuration, 512 samples (two workspace chunks at L = 24)
-    w = inputs.WORKLOADS["L24_bf16_sr"]
-    sig, theta = inputs.workload_inputs(w, batch=512)
-    ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, "bf16")
-    ctx.set_params(torch.tensor(theta, device="cuda"))
-    s = torch.tensor(sig, device="cuda")
-    _, nn = ctx.local_energy_sym(s)
-    torch.cuda.synchronize()
-    a, b = ev(), ev()
-    a.record(stream)
-    ctx.local_energy_sym(s, n_nbr=False)
-    b.record(stream)
-    torch.cuda.synchronize()
-    t = a.elapsed_time(b)
-    ncfg = 4 * int(512 + nn.sum().item())
-    out["eloc_sym_L24_bf16"] = {"samples": 512, "ms": t, "samples_per_s": 512 / (t / 1e3),
-                                "forward_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (t / 1e3) / 1e12,
-                                "launches": ctx.last_launch_count}
-    ctx.close()
-    torch.cuda.empty_cache()
-    # batched Metropolis transitions (vmc_metropolis): one forward per chain
-    # per transition, B chains advancing together
-    for name, B, steps in (("L16_bf16", 8192, 8), ("L24_bf16_sr", 4096, 8)):
-        w = inputs.WORKLOADS[name]
-        sig, theta = inputs.workload_inputs(w, batch=B)
-        u = torch.tensor(inputs.chain_uniforms(steps, B, inputs.rng_for(w.index, 11)), device="cuda")
+        t_r = a.elapsed_time(b)
+        per_L = {}
+        t_split = 0.0
+        for L in w.Ls:
+            idx = np.flatnonzero(Ls == L)
+            sig = np.stack([packed[offs[i]:offs[i] + L * L] for i in idx]).reshape(-1, L, L)
+            cl = VMC(int(L), w.J1, w.J2, w.C, w.D, w.precision)
+            cl.set_params(torch.tensor(theta, device="cuda"))
+            sL = torch.tensor(sig, device="cuda")
+            eL = torch.empty(len(idx), dtype=torch.float64, device="cuda")
+            cl.local_energy(sL, out=eL, n_nbr=False)
+            torch.cuda.synchronize()
+            a, b = ev(), ev()
+            a.record(stream)
+            cl.local_energy(sL, out=eL, n_nbr=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tL = a.elapsed_time(b)
+            t_split += tL
+            fl = float(sum((1.0 + float(k)) for k in nn.cpu().numpy()[idx])) * f_fwd(int(L), w.C, w.D)
+            per_L[str(int(L))] = {"samples": int(len(idx)), "ms": tL, "tflops": fl / (tL / 1e3) / 1e12}
+            cl.close()
+        out["ragged_8_16_fp16"] = {"samples": B, "ms": t_r, "samples_per_s": B / (t_r / 1e3),
+                                   "eloc_tflops": flops / (t_r / 1e3) / 1e12, "launch": "one persistent launch, CUDA graph",
+                                   "per_L_separate_launches": per_L, "separate_total_ms": t_split}
+        ctx.close()
+        torch.cuda.empty_cache()
+    if "sym" in parts:
+        # rotationally symmetrised local energy (vmc_local_energy_sym): four
+        # forwards per configuration, 512 samples (two workspace chunks at L = 24)
+        w = inputs.WORKLOADS["L24_bf16_sr"]
+        sig, theta = inputs.workload_inputs(w, batch=512)
         ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, "bf16")
         ctx.set_params(torch.tensor(theta, device="cuda"))
         s = torch.tensor(sig, device="cuda")
-        la, _ = ctx.logpsi(s)
-        acc = torch.zeros(B, dtype=torch.int32, device="cuda")
-        ctx.metropolis(s, la, u[:1], accepted=acc)
+        _, nn = ctx.local_energy_sym(s)
         torch.cuda.synchronize()
-        acc.zero_()
         a, b = ev(), ev()
         a.record(stream)
-        ctx.metropolis(s, la, u, accepted=acc)
+        ctx.local_energy_sym(s, n_nbr=False)
         b.record(stream)
         torch.cuda.synchronize()
         t = a.elapsed_time(b)
-        out[f"mcmc_L{w.L}_bf16"] = {"transitions_per_s": B * steps / (t / 1e3), "chains": B, "steps": steps,
-                                    "ms": t, "acceptance": float(acc.sum().item()) / (B * steps),
-                                    "forward_tflops": B * steps * f_fwd(w.L, w.C, w.D) / (t / 1e3) / 1e12,
-                                    "sweep_ms": t * w.L * w.L / steps,
+        ncfg = 4 * int(512 + nn.sum().item())
+        out["eloc_sym_L24_bf16"] = {"samples": 512, "ms": t, "samples_per_s": 512 / (t / 1e3),
+                                    "forward_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (t / 1e3) / 1e12,
                                     "launches": ctx.last_launch_count}
         ctx.close()
         torch.cuda.empty_cache()
+    if "mcmc" in parts:
+        # batched Metropolis transitions (vmc_metropolis): one forward per chain
+        # per transition, B chains advancing together
+        for name, B, steps in (("L16_bf16", 8192, 8), ("L24_bf16_sr", 4096, 8)):
+            w = inputs.WORKLOADS[name]
+            sig, theta = inputs.workload_inputs(w, batch=B)
+            u = torch.tensor(inputs.chain_uniforms(steps, B, inputs.rng_for(w.index, 11)), device="cuda")
+            ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, "bf16")
+            ctx.set_params(torch.tensor(theta, device="cuda"))
+            s = torch.tensor(sig, device="cuda")
+            la, _ = ctx.logpsi(s)
+            acc = torch.zeros(B, dtype=torch.int32, device="cuda")
+            ctx.metropolis(s, la, u[:1], accepted=acc)
+            torch.cuda.synchronize()
+            acc.zero_()
+            a, b = ev(), ev()
+            a.record(stream)
+            ctx.metropolis(s, la, u, accepted=acc)
+            b.record(stream)
+            torch.cuda.synchronize()
+            t = a.elapsed_time(b)
+            out[f"mcmc_L{w.L}_bf16"] = {"transitions_per_s": B * steps / (t / 1e3), "chains": B, "steps": steps,
+                                        "ms": t, "acceptance": float(acc.sum().item()) / (B * steps),
+                                        "forward_tflops": B * steps * f_fwd(w.L, w.C, w.D) / (t / 1e3) / 1e12,
+                                        "sweep_ms": t * w.L * w.L / steps,
+                                        "launches": ctx.last_launch_count}
+            ctx.close()
+            torch.cuda.empty_cache()
     return out
 
 
