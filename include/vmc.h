@@ -126,8 +126,8 @@ int vmc_local_energy_ragged(vmc_ctx *ctx, const int8_t *packed_dev, const int64_
                             const int32_t *L_dev, int64_t B, int L_max,
                             double *eloc_dev, int32_t *n_nbr_dev, void *stream);
 
-/* Rotationally symmetrised amplitude (Sec. 2.2, the equation after Eq. 9;
- * Sec. 3.4 applies it in the last fine-tuning stage):
+/* Rotationally symmetrised amplitude (Sec. 2.2, Eq. 10; Sec. 3.3 applies it
+ * in the last fine-tuning stage):
  *     W~(S) = sum_{i=0..3} W(T^i S),  W = (-1)^{M_A} W_CNN,
  * T the 90-degree rotation of the L x L lattice.  Each W~ evaluates the
  * context's forward (the arithmetic of vmc_logpsi, signs included) on the

@@ -3,13 +3,13 @@
 Only the tests, `__graft_entry__.smoke()` and the CPU-baseline leg of
 `bench.py` may import this module; it shares no code with the CUDA library.
 
-Sec. 2.2 of arXiv:2108.13830 (the equation after Eq. 9) enforces the
+Sec. 2.2 of arXiv:2108.13830 (Eq. 10) enforces the
 rotational symmetry of the ground state by summing the amplitude over the
 four 90-degree rotations T of the L x L lattice:
 
     W~(S) = sum_{i=0..3} W(T^i S),   W(S) = (-1)^{M_A} W_CNN(S).
 
-Sec. 3.4 applies it in the last fine-tuning stage at four times the cost.
+Sec. 3.3 applies it in the last fine-tuning stage at four times the cost.
 Here:
  - log|W~| and sgn W~ come from the four signed amplitudes, summed in FP64
    after factoring out the largest |W(T^i S)|;

@@ -1,5 +1,5 @@
-// Rotationally symmetrised amplitude (arXiv:2108.13830 Sec. 2.2, the
-// equation after Eq. 9; Sec. 3.4 applies it in the last fine-tuning stage):
+// Rotationally symmetrised amplitude (arXiv:2108.13830 Sec. 2.2, Eq. 10;
+// Sec. 3.3 applies it in the last fine-tuning stage):
 // W~(S) = sum_{i=0..3} W(T^i S), T the 90-degree rotation of the L x L
 // lattice, W = (-1)^{M_A} W_CNN.
 //

@@ -1,6 +1,6 @@
 """Parity of the rotationally symmetrised amplitude W~(S) = sum_i W(T^i S)
 (vmc_logpsi_sym, vmc_local_energy_sym, vmc_log_derivs_sym; Sec. 2.2 and
-Sec. 3.4) with the oracle and with its own definition.
+Sec. 3.3) with the oracle and with its own definition.
 
 FP64, L = 4 (C = 4, D = 2): log|W~|, sgn W~, E_loc and O_k against the
 oracle to FP64 rounding.

@@ -1,6 +1,6 @@
 """Pins for the oracle's rotationally symmetrised amplitude
-W~(S) = sum_{i=0..3} W(T^i S) (Sec. 2.2, the equation after Eq. 9;
-Sec. 3.4) against facts fixed by mathematics.  Nothing here uses the CUDA
+W~(S) = sum_{i=0..3} W(T^i S) (Sec. 2.2, Eq. 10; Sec. 3.3) against facts
+fixed by mathematics.  Nothing here uses the CUDA
 library.
 """
 import numpy as np

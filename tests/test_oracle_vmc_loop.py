@@ -1,6 +1,6 @@
 """The whole method on the oracle, pinned by exact diagonalisation: 40 SR
 iterations on the 4 x 4 lattice at J2 = 0.5 (Sec. 2-3: Metropolis samples of
-512 chains, L^2 transitions apart, E_loc, O_k, the CG solve of
+512 chains, L^2 transitions apart (Sec. 3.1), E_loc, O_k, the CG solve of
 (S + shift I) x = G and the update theta - eta x of Eq. 6) take the exact
 variational energy of the CNN from its random-initialisation value to
 within 0.02 per site of the ground-state energy E0 = -8.457923 (the
