@@ -5,7 +5,7 @@ the local energy and O_k, so no collective touches the data path.  The only
 communication is timing: a barrier on both sides of the timed region and
 the maximum elapsed time over ranks.  The SR solve stays per rank (its S v
 would need an all-reduce of an n-vector per CG step to pool the ranks'
-samples; that exchange is not part of this build).
+samples; the library has no such exchange).
 """
 from __future__ import annotations
 
