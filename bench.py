@@ -201,7 +201,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="L24_bf16_sr", choices=sorted(inputs.WORKLOADS))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--no-also", action="store_true", help="skip the L=16 / FP32 side measurements")
+    ap.add_argument("--no-also", action="store_true", help="skip the side measurements (L = 16, FP32, ragged, symmetrised, sampler)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--eloc-only", action="store_true",
                     help="profiling case: only the local-energy launch, no JSON contract line")
