@@ -3,8 +3,9 @@
 Only the tests, `__graft_entry__.smoke()` and the CPU-baseline leg of
 `bench.py` may import this package.  It shares no code with the CUDA
 library: the C part (oracle.c) is compiled by oracle/build.py with gcc and
-loaded through ctypes; the exact-diagonalisation and dense-solve pins live
-in ed.py / dense.py on top of numpy/scipy.
+loaded through ctypes; exact diagonalisation (ed.py), the Metropolis chain
+(metropolis.py) and the rotational symmetrisation (symmetry.py) sit on top of
+numpy/scipy.
 
 Functions follow the paper (arXiv:2108.13830): Hamiltonian Eq. 3, local
 energy Eq. 4-5, Marshall sign Eq. 9, O_k Eq. 5, covariance Eq. 7 with the

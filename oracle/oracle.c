@@ -59,6 +59,13 @@ static void cnn_forward(int L, int C, int D, const double *theta, const int8_t *
 {
     const int N = L * L;
     double *a = (double *)malloc(sizeof(double) * (size_t)C * N);
+    /* site of tap (ky, kx) around each site, t = 3 ky + kx, mod L */
+    int *nbr = (int *)malloc(sizeof(int) * 9 * (size_t)N);
+    for (int y = 0; y < L; ++y)
+        for (int x = 0; x < L; ++x)
+            for (int ky = 0; ky < 3; ++ky)
+                for (int kx = 0; kx < 3; ++kx)
+                    nbr[9 * (y * L + x) + 3 * ky + kx] = ((y + ky - 1 + L) % L) * L + (x + kx - 1 + L) % L;
     for (int l = 0; l <= D; ++l) {
         const int cin = (l == 0) ? 1 : C;
         const double *W = theta + w_offset(C, l);
@@ -71,17 +78,20 @@ static void cnn_forward(int L, int C, int D, const double *theta, const int8_t *
         for (int co = 0; co < C; ++co)
             for (int y = 0; y < L; ++y)
                 for (int x = 0; x < L; ++x) {
+                    const int *nb = nbr + 9 * (y * L + x);
                     double acc = b[co];
-                    for (int ci = 0; ci < cin; ++ci)
-                        for (int ky = 0; ky < 3; ++ky)
-                            for (int kx = 0; kx < 3; ++kx) {
-                                int yy = (y + ky - 1 + L) % L, xx = (x + kx - 1 + L) % L;
-                                double in = (l == 0) ? (double)s[yy * L + xx] : a[ci * N + yy * L + xx];
-                                acc += W[((co * cin + ci) * 3 + ky) * 3 + kx] * in;
-                            }
+                    for (int ci = 0; ci < cin; ++ci) {
+                        const double *Wc = W + (co * cin + ci) * 9;
+                        const double *ac = a + (size_t)ci * N;
+                        for (int t = 0; t < 9; ++t) {
+                            const double in = (l == 0) ? (double)s[nb[t]] : ac[nb[t]];
+                            acc += Wc[t] * in;
+                        }
+                    }
                     zl[co * N + y * L + x] = acc;
                 }
     }
+    free(nbr);
     free(a);
 }
 
