@@ -220,11 +220,16 @@ int vmc_ot_vec(vmc_ctx *ctx, const float *O_dev, int64_t m, const double *w_dev,
  *    owned by the caller); asynchronous on `stream`.
  *  - Limit: 8 n c + 8 m <= 16 MiB (m rounded up to a multiple of 32), with
  *    c = 16 row chunks for m >= 1024, 4 for m >= 64, else 1; e.g. m = 4096
- *    allows n <= 130816.  Larger sizes return VMC_ERR_UNSUPPORTED before
- *    any device work; null pointers or m, n < 1 return VMC_ERR_ARG.
- *  - The first call on a device looks up the scratch array's device address
- *    (with that device current) and caches it; make that first call before
- *    any stream capture.
+ *    allows n <= 130816, m = 1 allows n <= 2097120.  Larger sizes return
+ *    VMC_ERR_UNSUPPORTED before any device work; null pointers or m, n < 1
+ *    return VMC_ERR_ARG.
+ *  - Every call looks up the scratch array's device address with the
+ *    caller's device and context current (nothing is cached, so a
+ *    cudaDeviceReset or a different driver context is safe).  With lazy
+ *    module loading (the CUDA default) the FIRST call on a device loads the
+ *    library's device module, which is when the driver reserves the 16 MiB;
+ *    make that first call at start-up, outside any allocator hook and before
+ *    any stream capture (a call with m = n = 1 serves as a warm-up).
  *  - All calls on a device share the scratch and it keeps the last call's
  *    contents (nothing in it needs to start at zero); calls whose work
  *    overlaps on the GPU (different streams, no ordering) race. */

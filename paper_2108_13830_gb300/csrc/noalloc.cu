@@ -11,7 +11,6 @@
 // The arithmetic is that of vmc_ot_vec: w is split into FP32 (hi, lo) pairs,
 // each CTA column block accumulates sum_b O_bk (hi_b + lo_b) over one chunk of
 // rows in double-float, and the chunk partials are summed in FP64.
-#include <mutex>
 #include "vmc_internal.h"
 
 // Scratch shared by every call on a device: the split w (2 m floats) followed
@@ -21,10 +20,6 @@
 static __device__ __align__(256) unsigned char g_ot_scratch[VMC_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {nullptr};
 
 __device__ __forceinline__ void na_two_sum(float a, float b, float &s, float &e)
 {
@@ -82,25 +77,20 @@ extern "C" int vmc_ot_vec_noalloc(const float *O_dev, int64_t m, int64_t n, cons
                                   double *out_dev, void *stream)
 {
     if (!O_dev || !w_dev || !out_dev || m < 1 || n < 1) return VMC_ERR_ARG;
+    // beyond the fixed scratch: refuse before any byte arithmetic (which could
+    // wrap for huge m or n) and before touching the device
+    const int64_t cap = (int64_t)VMC_NOALLOC_SCRATCH_BYTES;
+    if (m > cap / 8 || n > cap / 8) return VMC_ERR_UNSUPPORTED;
     const int64_t nchunk = m >= 1024 ? 16 : (m >= 64 ? 4 : 1);
-    const size_t w_bytes = ((size_t)(2 * m) * sizeof(float) + 255) & ~(size_t)255;
-    // beyond the fixed scratch: refuse before touching the device
-    if ((double)w_bytes + (double)nchunk * (double)n * 8.0 > (double)VMC_NOALLOC_SCRATCH_BYTES)
-        return VMC_ERR_UNSUPPORTED;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VMC_ERR_CUDA;
+    const int64_t w_bytes = (2 * m * (int64_t)sizeof(float) + 255) & ~(int64_t)255;
+    if (w_bytes + nchunk * n * 8 > cap) return VMC_ERR_UNSUPPORTED;
+    // The device address of the scratch array, looked up on every call with
+    // the caller's device and context current (the host-side symbol is only
+    // a stand-in).  Once the module is loaded this allocates nothing; a
+    // cached address would go stale after cudaDeviceReset or under another
+    // driver-API context, each of which has its own copy of the array.
     void *base = nullptr;
-    {
-        // once per device, with that device current: the device address of
-        // the scratch array (the host-side symbol is only a stand-in)
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_ot_scratch) != cudaSuccess || !p) return VMC_ERR_CUDA;
-            g_scratch_ptr[dev] = p;
-        }
-        base = g_scratch_ptr[dev];
-    }
+    if (cudaGetSymbolAddress(&base, g_ot_scratch) != cudaSuccess || !base) return VMC_ERR_CUDA;
     char *b = static_cast<char *>(base);
     float *wh = reinterpret_cast<float *>(b);
     float *wl = wh + m;
