@@ -31,22 +31,21 @@ sys.path.insert(0, ROOT)
 from paper_2108_13830_gb300 import inputs, replicas  # noqa: E402
 
 
-def tc_traffic(samples):
-    """DRAM bytes of one tensor-core E_loc launch over `samples` samples, from
-    the ncu capture summarised in profiles/tc_eloc_L24_dram.md (scaled by the
-    sample count, which the traffic grows with), or None once the kernel
-    source differs from the one the counters were taken on."""
+def tc_traffic(key, samples):
+    """DRAM bytes of one launch over `samples` samples from the ncu figures in
+    profiles/dram_traffic.json (entry `key`, scaled by the sample count, which
+    the traffic grows with), or None once the kernel source differs from the
+    one the counters were taken on."""
     import hashlib
-    import re
-    path = os.path.join(ROOT, "profiles", "tc_eloc_L24_dram.md")
-    src = os.path.join(ROOT, "paper_2108_13830_gb300", "csrc", "tc_fwd.cu")
     try:
-        m = re.search(r"traffic: kernel=\S+ sha256=([0-9a-f]{64}) samples=(\d+) dram_bytes=(\d+)", open(path).read())
-        if not m or hashlib.sha256(open(src, "rb").read()).hexdigest() != m.group(1):
+        d = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))[key]
+        src = os.path.join(ROOT, d["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != d["source_sha256"]:
             return None
-        return int(m.group(3)) * samples / int(m.group(2))
-    except OSError:
+        return d["dram_bytes"] * samples / d["samples"]
+    except (OSError, KeyError, ValueError):
         return None
+
 
 METRIC = "E_loc+O_k samples/sec at L=16,24 (BF16-TC vs FP32 plain); roofline %"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
@@ -320,7 +319,7 @@ def main():
     peak_t = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
     eloc_mean = statistics.mean(eloc_ms)
     achieved = flops_eloc / (eloc_mean / 1e3) / 1e12
-    traffic = tc_traffic(B) if w.name == "L24_bf16_sr" else None
+    traffic = tc_traffic("tc_eloc_kernel<32,BF16,3> L=24", B) if w.name == "L24_bf16_sr" else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
                 "frac": achieved / peak_t, "traffic": traffic, "kernel": "tc_eloc_kernel<32>",
                 "peak_source": f"{peak_src} bf16_tflops_sustained",
@@ -381,13 +380,17 @@ SIDE_PARTS = ("eloc", "ragged", "sym", "mcmc")
 
 
 def side_measurements(torch, VMC, ev, stream, parts=SIDE_PARTS):
-    """E_loc + O_k samples/s at L = 16 and L = 24 for the BF16 tensor-core and
-    the plain FP32 paths (FP32 on a sub-batch to bound the run time), and
+    """E_loc + O_k samples/s at L = 16 and L = 24 for the BF16 and FP16
+    tensor-core and the plain FP32 paths (FP32 on a sub-batch to bound the
+    run time), and
     the transition rate of the batched Metropolis sampler."""
     out = {}
     if "eloc" in parts:
-        for name, prec, B in (("L16_bf16", "bf16", 8192), ("L16_bf16", "fp32", 256),
-                              ("L24_bf16_sr", "bf16", 4096), ("L24_bf16_sr", "fp32", 64)):
+        # FP16 operands are the 16-bit arm that meets the 5e-4 per-site E_loc
+        # bound at L = 16 as well (BF16 meets it at L = 24)
+        for name, prec, B in (("L16_bf16", "bf16", 8192), ("L16_bf16", "fp16", 8192), ("L16_bf16", "fp32", 256),
+                              ("L24_bf16_sr", "bf16", 4096), ("L24_bf16_sr", "fp16", 4096),
+                              ("L24_bf16_sr", "fp32", 64)):
             w = inputs.WORKLOADS[name]
             sig, theta = inputs.workload_inputs(w, batch=B)
             ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, prec)
