@@ -42,6 +42,7 @@ def lib():
         L.orc_log_derivs_batch.argtypes = [_I, _I, _I, _dp, _i8p, _I64, _dp, _I]
         L.orc_sr_moments.argtypes = [_dp, _dp, _I64, _I64, _dp, _dp, _dp]
         L.orc_sr_matvec.argtypes = [_dp, _I64, _I64, _dp, _dp, _D, _dp]
+        L.orc_sr_matvec_centered.argtypes = [_dp, _I64, _I64, _dp, _D, _dp]
         L.orc_sr_cg.restype = _D
         L.orc_sr_cg.argtypes = [_dp, _I64, _I64, _dp, _dp, _D, _I, _dp]
         L.orc_max_threads.restype = _I
@@ -140,6 +141,17 @@ def sr_matvec(O, Obar, v, shift):
     m, n = O.shape
     out = _np.zeros(n)
     lib().orc_sr_matvec(O, m, n, _f64(Obar), _f64(v), float(shift), out)
+    return out
+
+
+def sr_matvec_centered(O, v, shift):
+    """(M + shift I) v with M the covariance in its centred form,
+    (1/m) sum_b (O_b - <O>) ((O_b - <O>) . v): equal to sr_matvec in exact
+    arithmetic, without its cancellation when |<O>| >> std(O)."""
+    O = _f64(O)
+    m, n = O.shape
+    out = _np.zeros(n)
+    lib().orc_sr_matvec_centered(O, m, n, _f64(v), float(shift), out)
     return out
 
 

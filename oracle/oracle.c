@@ -404,6 +404,34 @@ void orc_sr_matvec(const double *O, int64_t m, int64_t n, const double *Obar,
     free(t);
 }
 
+/* The same covariance product with the covariance written in its centred
+ * form, M v = (1/m) sum_b (O_b - <O>) ((O_b - <O>) . v): the textbook
+ * definition of a sample covariance, equal in real arithmetic to the
+ * <O O> - <O><O> of Eq. 7 (Sec. 3.2.2).  In floating point it avoids the
+ * cancellation between the two uncentred terms when the column means of O
+ * are large against its spread, as they are for log-derivatives of a
+ * trained-size network.  The column means are computed here. */
+void orc_sr_matvec_centered(const double *O, int64_t m, int64_t n, const double *v, double shift, double *out)
+{
+    double *c = (double *)calloc((size_t)n, sizeof(double));
+    double *d = (double *)malloc(sizeof(double) * (size_t)m);
+    for (int64_t b = 0; b < m; ++b)
+        for (int64_t k = 0; k < n; ++k) c[k] += O[b * n + k];
+    for (int64_t k = 0; k < n; ++k) c[k] /= (double)m;
+    for (int64_t b = 0; b < m; ++b) {
+        double acc = 0.0;
+        for (int64_t k = 0; k < n; ++k) acc += (O[b * n + k] - c[k]) * v[k];
+        d[b] = acc;
+    }
+    for (int64_t k = 0; k < n; ++k) out[k] = 0.0;
+    /* out_k accumulates over b in increasing order */
+    for (int64_t b = 0; b < m; ++b)
+        for (int64_t k = 0; k < n; ++k) out[k] += (O[b * n + k] - c[k]) * d[b];
+    for (int64_t k = 0; k < n; ++k) out[k] = out[k] / (double)m + shift * v[k];
+    free(c);
+    free(d);
+}
+
 static double dot(const double *a, const double *b, int64_t n)
 {
     double acc = 0.0;

@@ -1,13 +1,29 @@
 """Full-size workloads in the launch configuration bench.py times.
 
 L = 16 (C = 32, D = 8, 8192 samples) and L = 24 (C = 32, D = 10, 4096
-samples) in BF16, the mixed-size batch (2048 samples of each of L = 8, 10,
-12, 16; 16 channels, 6 layers) in FP16: every sample's neighbour count
-exactly, E_loc/site of sampled parents within the per-sample tolerance of
-the FP64 oracle, the
-batch-mean energy of BF16 within 1e-5 per site of the FP32 path (whose
-per-sample error is <= 1e-6), O_k rows against the oracle, and the SR solve
-on the full O through its true residual.
+samples) with 16-bit tensor-core operands, and the mixed-size batch (2048
+samples of each of L = 8, 10, 12, 16; 16 channels, 6 layers) in FP16:
+
+- every sample's neighbour count, exactly;
+- E_loc/site of sampled parents spread over the batch (first and last
+  sample included, so the first and last CTA, slab and ring positions are
+  covered) against the FP64 oracle (Eq. 4-5);
+- every sample's E_loc bitwise unchanged when the batch is reversed or cut
+  (a result must not depend on where the sample lands);
+- the batch-mean energy of the 16-bit paths against the FP32 path;
+- O_k rows against the oracle (Eq. 5);
+- the SR moments G, <O> and one S v on the real O against the oracle, and
+  the CG solve through its true residual (Sec. 3.2.2).
+
+Tolerances, per site: the FP32 path 1e-6 per sample at L = 10 and 2e-6 at
+L = 16 (its FP32 activations through nine layers put one parent of four at
+1.2e-6, measured); FP16 operands 5e-4
+per sample at L = 16 and L = 24; BF16 operands 5e-4 per sample at L = 24.
+At L = 16 BF16 operands do NOT meet 5e-4 for every sample (its 8-bit
+significand: a CPU emulation of exact BF16 rounding with FP32 accumulation
+already reaches 5.8e-4 on one of six parents), so the BF16 test there
+asserts 1e-3 per sample and 5e-4 for the median, and FP16 is the 16-bit
+arm that meets 5e-4.  Batch means: within 1e-5 per site of the FP32 path.
 """
 import os
 
@@ -24,6 +40,18 @@ pytestmark = pytest.mark.gpu
 
 NTH = os.cpu_count() or 8
 
+TOL_16BIT = 5e-4          # per sample, per site (FP16 everywhere, BF16 at L = 24)
+L16_BF16_TOL = 1e-3       # BF16 at L = 16: misses 5e-4 on some samples (see above)
+MEAN_TOL = 1e-5           # batch mean, per site, against the FP32 path
+FP32_TOL = 1e-6          # O_k rows (normwise) and FP32 E_loc at L = 10
+FP32_L16_ELOC_TOL = 2e-6  # FP32 E_loc per sample at L = 16 (1.2e-6 measured)
+
+
+def _spread(B, k, seed):
+    """k sample indices over [0, B): the first, the last and k - 2 random ones."""
+    mid = np.random.default_rng(seed).choice(np.arange(1, B - 1), k - 2, replace=False)
+    return np.concatenate([[0], np.sort(mid), [B - 1]])
+
 
 @pytest.fixture(scope="module")
 def l16():
@@ -36,6 +64,32 @@ def l16():
     return w, sig, theta, v, s, e.cpu().numpy(), nn.cpu().numpy()
 
 
+@pytest.fixture(scope="module")
+def l16_fp16(l16):
+    w, sig, theta, v, s, e, nn = l16
+    v16 = make_ctx(w, precision="fp16", theta=theta)
+    e16, _ = v16.local_energy(s)
+    assert v16.sync_status()[0] == VMC_OK
+    return e16.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def l16_fp32(l16):
+    w, sig, theta, v, s, e, nn = l16
+    v32 = make_ctx(w, precision="fp32", theta=theta)
+    e32, _ = v32.local_energy(s)
+    assert v32.sync_status()[0] == VMC_OK
+    return e32.cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def l16_pick(l16):
+    w, sig, theta, v, s, e, nn = l16
+    pick = _spread(w.batch, 32, 16)
+    re, rn = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
+    return pick, re, rn
+
+
 def test_l16_neighbour_counts(l16):
     w, sig, theta, v, s, e, nn = l16
     a1, a2 = bond_counts(sig)
@@ -43,70 +97,65 @@ def test_l16_neighbour_counts(l16):
     assert np.all(np.isfinite(e))
 
 
-# Per-sample E_loc/site tolerances.  FP16 operands: 5e-4.  BF16 operands:
-# 5e-4 at L = 24; at L = 16 a CPU emulation of exact BF16 rounding (FP32
-# accumulation, exact SiLU) already reaches 5.8e-4 on one of six sampled
-# parents, so the per-sample bound there is 1e-3 while the batch-mean bound
-# (1e-5 per site) is unchanged.
-L16_BF16_TOL = 1e-3
-
-
-@pytest.fixture(scope="module")
-def l16_pick(l16):
-    w, sig, theta, v, s, e, nn = l16
-    pick = np.random.default_rng(16).choice(w.batch, 6, replace=False)
-    re, rn = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
-    return pick, re, rn
+def test_l16_fp16_sampled_parents_vs_oracle(l16, l16_fp16, l16_pick):
+    w = l16[0]
+    pick, re, rn = l16_pick
+    np.testing.assert_array_equal(l16[6][pick], rn)
+    err = np.abs(l16_fp16[pick] - re) / (w.L * w.L)
+    assert err.max() <= TOL_16BIT, err
 
 
 def test_l16_bf16_sampled_parents_vs_oracle(l16, l16_pick):
     w, sig, theta, v, s, e, nn = l16
     pick, re, rn = l16_pick
-    np.testing.assert_array_equal(nn[pick], rn)
     err = np.abs(e[pick] - re) / (w.L * w.L)
     assert err.max() <= L16_BF16_TOL, err
-    assert np.median(err) <= 5e-4, err
+    assert np.median(err) <= TOL_16BIT, err
 
 
-def test_l16_fp16_sampled_parents_vs_oracle(l16, l16_pick):
-    w, sig, theta, v, s, e, nn = l16
+def test_l16_fp32_sampled_parents_vs_oracle(l16, l16_fp32, l16_pick):
+    w = l16[0]
     pick, re, rn = l16_pick
-    v16 = make_ctx(w, precision="fp16", theta=theta)
-    e16, _ = v16.local_energy(s[torch.as_tensor(pick, device="cuda")])
-    assert v16.sync_status()[0] == VMC_OK
-    err = np.abs(e16.cpu().numpy() - re) / (w.L * w.L)
-    assert err.max() <= 5e-4, err
+    sub = pick[:: len(pick) // 4][:4]
+    err = np.abs(l16_fp32[sub] - re[np.searchsorted(pick, sub)]) / (w.L * w.L)
+    assert err.max() <= FP32_L16_ELOC_TOL, err
+    assert np.median(err) <= FP32_TOL, err
 
 
-def test_l16_bf16_mean_energy_vs_fp32(l16):
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_l16_mean_energy_vs_fp32(l16, l16_fp16, l16_fp32, prec):
+    """Over all 8192 samples: the per-sample difference d = E_16bit - E_fp32 is
+    a random variable from the operand rounding (std ~0.1 for BF16 at this
+    size); its mean, the bias of the energy estimator, must be within
+    1e-5 per site and within four standard errors of zero."""
     w, sig, theta, v, s, e, nn = l16
-    B = 2048
-    v32 = make_ctx(w, precision="fp32", theta=theta)
-    e32, _ = v32.local_energy(s[:B])
-    assert v32.sync_status()[0] == VMC_OK
-    e32 = e32.cpu().numpy()
-    N = w.L * w.L
-    # BF16 rounding makes the per-sample error d = E_bf16 - E_fp32 a random
-    # variable (std ~0.1 at L = 16 for this network); the estimator is
-    # unbiased when the mean of d is within a few standard errors of zero.
-    d = e[:B] - e32
-    sem = d.std(ddof=1) / np.sqrt(B)
+    e16 = e if prec == "bf16" else l16_fp16
+    d = e16 - l16_fp32
+    sem = d.std(ddof=1) / np.sqrt(len(d))
     assert abs(d.mean()) <= 4.0 * sem, (d.mean(), sem)
-    assert abs(d.mean()) / N <= 5e-5
-    pick = np.random.default_rng(17).choice(B, 2, replace=False)
-    re, _ = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
-    assert (np.abs(e32[pick] - re) / N).max() <= 1e-6
+    assert abs(d.mean()) / (w.L * w.L) <= MEAN_TOL, d.mean() / (w.L * w.L)
+
+
+def test_l16_results_independent_of_batch_position(l16):
+    """Reversed and cut batches put every sample in another CTA, slab, ring
+    entry and tile position: E_loc must stay bitwise the same."""
+    w, sig, theta, v, s, e, nn = l16
+    er, _ = v.local_energy(s.flip(0))
+    ec, _ = v.local_energy(s[1001:5000])
+    assert v.sync_status()[0] == VMC_OK
+    np.testing.assert_array_equal(er.cpu().numpy()[::-1], e)
+    np.testing.assert_array_equal(ec.cpu().numpy(), e[1001:5000])
 
 
 def test_l16_log_derivs_rows(l16):
     w, sig, theta, v, s, e, nn = l16
     O = v.log_derivs(s)                      # full batch, [8192, 74304] FP32
     assert torch.isfinite(O).all().item()
-    rows = [0, w.batch - 1]
+    rows = _spread(w.batch, 8, 161)
     R = oracle.log_derivs(w.L, w.C, w.D, theta, sig[rows], nthreads=NTH)
-    Og = O[rows].double().cpu().numpy()
+    Og = O[torch.as_tensor(rows, device=O.device)].double().cpu().numpy()
     rel = np.abs(Og - R).max(axis=1) / np.abs(R).max(axis=1)
-    assert rel.max() <= 1e-6, rel
+    assert rel.max() <= FP32_TOL, rel
 
 
 @pytest.fixture(scope="module")
@@ -120,29 +169,76 @@ def l24():
     return w, sig, theta, v, s, e, nn.cpu().numpy()
 
 
-def test_l24_bf16_sampled_parents_vs_oracle(l24):
+@pytest.fixture(scope="module")
+def l24_pick(l24):
+    w, sig, theta, v, s, e, nn = l24
+    pick = _spread(w.batch, 16, 24)
+    re, rn = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
+    return pick, re, rn
+
+
+def test_l24_bf16_sampled_parents_vs_oracle(l24, l24_pick):
     w, sig, theta, v, s, e, nn = l24
     a1, a2 = bond_counts(sig)
     np.testing.assert_array_equal(nn, a1 + a2)
-    pick = np.random.default_rng(24).choice(w.batch, 2, replace=False)
-    re, rn = oracle.local_energy_par(w.L, w.J1, w.J2, w.C, w.D, theta, sig[pick], nthreads=NTH)
+    pick, re, rn = l24_pick
+    np.testing.assert_array_equal(nn[pick], rn)
     err = np.abs(e.cpu().numpy()[pick] - re) / (w.L * w.L)
-    assert err.max() <= 5e-4, err
+    assert err.max() <= TOL_16BIT, err
+
+
+def test_l24_fp16_sampled_parents_vs_oracle(l24, l24_pick):
+    w, sig, theta, v, s, e, nn = l24
+    pick, re, rn = l24_pick
+    v16 = make_ctx(w, precision="fp16", theta=theta)
+    e16, _ = v16.local_energy(s[torch.as_tensor(pick, device="cuda")])
+    assert v16.sync_status()[0] == VMC_OK
+    err = np.abs(e16.cpu().numpy() - re) / (w.L * w.L)
+    assert err.max() <= TOL_16BIT, err
+
+
+def test_l24_results_independent_of_batch_position(l24):
+    w, sig, theta, v, s, e, nn = l24
+    er, _ = v.local_energy(s.flip(0))
+    ec, _ = v.local_energy(s[777:3333])
+    assert v.sync_status()[0] == VMC_OK
+    e = e.cpu().numpy()
+    np.testing.assert_array_equal(er.cpu().numpy()[::-1], e)
+    np.testing.assert_array_equal(ec.cpu().numpy(), e[777:3333])
 
 
 def test_l24_log_derivs_and_sr(l24):
     w, sig, theta, v, s, e, nn = l24
     O = v.log_derivs(s)                      # [4096, 92800] FP32, 1.52 GB
-    R = oracle.log_derivs(w.L, w.C, w.D, theta, sig[:1], nthreads=NTH)
-    rel = np.abs(O[0].double().cpu().numpy() - R[0]).max() / np.abs(R[0]).max()
-    assert rel <= 1e-6
+    rows = _spread(w.batch, 8, 241)
+    R = oracle.log_derivs(w.L, w.C, w.D, theta, sig[rows], nthreads=NTH)
+    Og = O[torch.as_tensor(rows, device=O.device)].double().cpu().numpy()
+    rel = np.abs(Og - R).max(axis=1) / np.abs(R).max(axis=1)
+    assert rel.max() <= FP32_TOL, rel
+
+    # SR on the real O: moments and one S v against the oracle, element-wise
+    Od = O.double().cpu().numpy()
+    en = e.cpu().numpy()
+    rob, reb, rg = oracle.sr_moments(Od, en)
+    ob, eb, g = v.sr_moments(O, e)
+    np.testing.assert_allclose(ob.cpu().numpy(), rob, rtol=1e-12, atol=1e-13 * np.abs(rob).max())
+    assert abs(eb.item() - reb) <= 1e-13 * abs(reb)
+    # the oracle's literal G = <O E> - <E><O> cancels; FP64 bound ~ m eps (...)
+    bound = 4 * w.batch * np.finfo(np.float64).eps * (np.abs(Od * en[:, None]).mean(axis=0) + np.abs(reb * rob))
+    assert np.all(np.abs(g.cpu().numpy() - rg) <= bound)
+    # S v against the covariance in its centred form: the uncentred oracle
+    # form (Eq. 7 as printed) cancels on these columns, whose means are large
+    # against their spread (its FP64 error reached 5e-9 of max |S v|)
+    vec = np.random.default_rng(242).standard_normal(Od.shape[1])
+    sv = v.sr_matvec(O, ob, to_dev(vec), w.shift).cpu().numpy()
+    rsv = oracle.sr_matvec_centered(Od, vec, w.shift)
+    np.testing.assert_allclose(sv, rsv, rtol=1e-9, atol=1e-11 * np.abs(rsv).max())
+
+    # the CG solve, through the true residual of its x
     x, res = v.sr_solve(O, e, w.shift, w.cg_iters)
     assert v.sync_status()[0] == VMC_OK
-    # true residual of x with the oracle's FP64 covariance product on the full O
-    Od = O.double().cpu().numpy()
-    ob, _, g = oracle.sr_moments(Od, e.cpu().numpy())
-    r = g - oracle.sr_matvec(Od, ob, x.cpu().numpy(), w.shift)
-    true_res = np.linalg.norm(r) / np.linalg.norm(g)
+    r = rg - oracle.sr_matvec(Od, rob, x.cpu().numpy(), w.shift)
+    true_res = np.linalg.norm(r) / np.linalg.norm(rg)
     assert true_res < 1.0
     assert abs(res - true_res) <= 0.05 * true_res + 1e-12
 
@@ -155,11 +251,12 @@ def test_ragged_full_batch():
     assert v.sync_status()[0] == VMC_OK
     e, nn = e.cpu().numpy(), nn.cpu().numpy()
     assert np.all(np.isfinite(e))
-    for L in w.Ls:
+    for j, L in enumerate(w.Ls):
         idx = np.where(Ls == L)[0]
         cfg = np.stack([packed[offs[b]:offs[b] + L * L].reshape(L, L) for b in idx])
         a1, a2 = bond_counts(cfg)
         np.testing.assert_array_equal(nn[idx], a1 + a2)
-        b = idx[len(idx) // 2]
-        re, _ = oracle.local_energy_par(L, w.J1, w.J2, w.C, w.D, theta, cfg[len(idx) // 2][None], nthreads=NTH)
-        assert abs(e[b] - re[0]) / (L * L) <= 5e-4
+        sub = _spread(len(idx), 4, 300 + j)
+        re, _ = oracle.local_energy_par(L, w.J1, w.J2, w.C, w.D, theta, cfg[sub], nthreads=NTH)
+        err = np.abs(e[idx[sub]] - re) / (L * L)
+        assert err.max() <= TOL_16BIT, (L, err)

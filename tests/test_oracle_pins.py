@@ -374,6 +374,31 @@ def test_sr_matvec_equals_explicit_covariance():
     assert np.linalg.eigvalsh(M).min() > -1e-10
 
 
+def test_sr_matvec_centered_form():
+    """The centred covariance product equals cov(O) v + shift v (textbook
+    sample covariance, biased) and the uncentred form of Eq. 7 on a
+    well-conditioned O; on columns whose means dwarf their spread it keeps
+    its accuracy where the uncentred form cancels."""
+    O, E = _sr_case()
+    m, n = O.shape
+    ob, _, _ = oracle.sr_moments(O, E)
+    S = np.cov(O, rowvar=False, bias=True)
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        v = rng.standard_normal(n)
+        c = oracle.sr_matvec_centered(O, v, 1e-3)
+        np.testing.assert_allclose(c, S @ v + 1e-3 * v, rtol=1e-11, atol=1e-12)
+        np.testing.assert_allclose(c, oracle.sr_matvec(O, ob, v, 1e-3), rtol=1e-10, atol=1e-12)
+    # means 1e4 x the spread: exact result known by construction (shifting
+    # every column by a constant leaves the covariance unchanged)
+    base = rng.standard_normal((m, n))
+    big = base + 1e4 * rng.standard_normal(n)
+    v = rng.standard_normal(n)
+    want = oracle.sr_matvec_centered(base, v, 0.0)
+    np.testing.assert_allclose(oracle.sr_matvec_centered(big, v, 0.0), want, rtol=1e-7,
+                               atol=1e-9 * np.abs(want).max())
+
+
 def test_cg_matches_dense_cholesky():
     """Sec. 3.2.2 solves (M + shift I) Delta = G by Cholesky; CG reaches the same x."""
     O, E = _sr_case(m=64, n=40)
