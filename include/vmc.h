@@ -265,6 +265,24 @@ int vmc_sync_status(vmc_ctx *ctx, void *stream, int64_t *nonfinite);
  * runs out sets VMC_ERR_TIMEOUT, releases its resources and returns. */
 int vmc_set_wait_budget(vmc_ctx *ctx, int64_t ns);
 
+/* Light-cone evaluation of the exchange neighbours in vmc_local_energy
+ * (tensor-core contexts, uniform batches).  The convolutions are 3 x 3
+ * (Sec. 2.2; the locality of the filters, Sec. 3.3), so after layer l the
+ * activations of a neighbour sigma' differ from its parent's only within
+ * l + 1 cells of the exchanged pair.  With it on, a first launch evaluates
+ * every parent and keeps all its layers' activations (workspace of
+ * 2 C D L^2 bytes per sample, up to 2 GiB, the batch taken in chunks
+ * beyond that); a second evaluates each neighbour on a window of side
+ * min(2 l + 4, L) per layer, filling the window's border from the parent.
+ * E_loc and the neighbour counts are bit for bit those of the plain
+ * evaluation.  It applies when 6 <= L <= 2 D + 4 (the window covers the
+ * lattice by the last layer); otherwise, for ragged batches and for
+ * FP32/FP64 contexts the plain evaluation runs.  On by default.
+ *  - vmc_set_light_cone: enable = 1 (default) or 0 (plain evaluation).
+ *  - vmc_light_cone_active: *active = 1 if vmc_local_energy uses it. */
+int vmc_set_light_cone(vmc_ctx *ctx, int enable);
+int vmc_light_cone_active(const vmc_ctx *ctx, int *active);
+
 /* Launch one wait on an mbarrier that nothing arrives on, with the given
  * budget; the wait must give up and report VMC_ERR_TIMEOUT through
  * vmc_sync_status.  Exercises the timeout path without faulting the GPU. */

@@ -63,6 +63,8 @@ _SIGS = {
     "vmc_sr_update": (_I, [_P, _P, _D, _P]),
     "vmc_sync_status": (_I, [_P, _P, ct.POINTER(_I64)]),
     "vmc_set_wait_budget": (_I, [_P, _I64]),
+    "vmc_set_light_cone": (_I, [_P, _I]),
+    "vmc_light_cone_active": (_I, [_P, _P]),
     "vmc_debug_wait_timeout": (_I, [_P, _I64, _P]),
     "vmc_set_tiles": (_I, [_P, _I, ct.POINTER(vmc_tiles)]),
     "vmc_get_tiles": (_I, [_P, _I, ct.POINTER(vmc_tiles)]),
@@ -284,6 +286,15 @@ class VMC:
 
     def set_wait_budget(self, ns):
         self._check(lib().vmc_set_wait_budget(self._h, int(ns)))
+
+    def set_light_cone(self, enable):
+        self._check(lib().vmc_set_light_cone(self._h, 1 if enable else 0))
+
+    @property
+    def light_cone_active(self):
+        a = ct.c_int(0)
+        self._check(lib().vmc_light_cone_active(self._h, ct.byref(a)))
+        return bool(a.value)
 
     def debug_wait_timeout(self, budget_ns):
         self._check(lib().vmc_debug_wait_timeout(self._h, int(budget_ns), _stream()))

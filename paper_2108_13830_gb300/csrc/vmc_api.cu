@@ -108,7 +108,7 @@ void vmc_destroy(vmc_ctx *ctx)
     cudaFree(ctx->theta64); cudaFree(ctx->theta32); cudaFree(ctx->wsimt); cudaFree(ctx->wsimtT);
     cudaFree(ctx->bias); cudaFree(ctx->bias32); cudaFree(ctx->wimg);
     cudaFree(ctx->status); cudaFree(ctx->counter);
-    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws); cudaFree(ctx->sym_ws); cudaFree(ctx->sym_cnt);
+    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws); cudaFree(ctx->sym_ws); cudaFree(ctx->sym_cnt); cudaFree(ctx->cone_ws);
     delete ctx;
 }
 
@@ -313,6 +313,20 @@ int vmc_set_wait_budget(vmc_ctx *ctx, int64_t ns)
 {
     if (!ctx || ns < 0) return VMC_ERR_ARG;
     ctx->wait_budget_ns = ns ? ns : 2000000000LL;
+    return VMC_OK;
+}
+
+int vmc_set_light_cone(vmc_ctx *ctx, int enable)
+{
+    if (!ctx || (enable != 0 && enable != 1)) return VMC_ERR_ARG;
+    ctx->light_cone = enable;
+    return VMC_OK;
+}
+
+int vmc_light_cone_active(const vmc_ctx *ctx, int *active)
+{
+    if (!ctx || !active) return VMC_ERR_ARG;
+    *active = (ctx->light_cone && vmc_tc_cone_applies(ctx)) ? 1 : 0;
     return VMC_OK;
 }
 

@@ -71,6 +71,9 @@ struct vmc_ctx {
     size_t sym_ws_bytes = 0;
     void *sym_cnt = nullptr;     // per-sample neighbour counts, diagonals, offsets
     size_t sym_cnt_bytes = 0;
+    void *cone_ws = nullptr;     // light-cone E_loc: parent activations, log|psi| and signs
+    size_t cone_ws_bytes = 0;
+    int light_cone = 1;          // evaluate E_loc neighbours incrementally where it applies
 
     int64_t wait_budget_ns = 2000000000LL;
     std::map<int, TileChoice> tiles;
@@ -111,6 +114,7 @@ int vmc_simt_log_derivs(vmc_ctx *ctx, const int8_t *sigma, int64_t B, void *O, i
 int vmc_tc_eloc(vmc_ctx *ctx, int mode, const int8_t *sigma, const int64_t *offs, const int32_t *Ls,
                 int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr, cudaStream_t s);
 int vmc_tc_default_tiles(const vmc_ctx *ctx, int L, TileChoice *t);
+bool vmc_tc_cone_applies(const vmc_ctx *ctx);
 int vmc_tc_debug_timeout(vmc_ctx *ctx, int64_t budget_ns, cudaStream_t s);
 
 // Metropolis sampling (mcmc.cu)
