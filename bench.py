@@ -56,6 +56,31 @@ def f_fwd(L, C, D):
     return 2.0 * L * L * (9 * C + 9 * D * C * C)
 
 
+def cone_flops(L, C, D, n_j1, n_j2):
+    """Algorithmic FLOPs of the light-cone evaluation of n_j1 J1 and n_j2 J2
+    exchange neighbours: after layer l only the cells within l + 1 of the
+    exchanged pair change (3 x 3 filters), a (2l+4) x (2l+3) box for a J1
+    pair and (2l+4)^2 for a J2 pair, each side capped at L; layer l costs
+    2 * 9 * c_in * C FLOPs per recomputed cell."""
+    f1 = f2 = 0.0
+    for l in range(D + 1):
+        cin = 1 if l == 0 else C
+        per_cell = 2.0 * 9 * cin * C
+        f1 += min(2 * l + 4, L) * min(2 * l + 3, L) * per_cell
+        f2 += min(2 * l + 4, L) ** 2 * per_cell
+    return n_j1 * f1 + n_j2 * f2
+
+
+def antiparallel_counts(sig):
+    """(J1, J2) antiparallel bond counts per configuration, by np.roll."""
+    s = sig.astype(np.int64)
+    right, down = np.roll(s, -1, axis=-1), np.roll(s, -1, axis=-2)
+    dr, dl = np.roll(down, -1, axis=-1), np.roll(down, 1, axis=-1)
+    a1 = np.sum(s * right == -1, axis=(-2, -1)) + np.sum(s * down == -1, axis=(-2, -1))
+    a2 = np.sum(s * dr == -1, axis=(-2, -1)) + np.sum(s * dl == -1, axis=(-2, -1))
+    return a1, a2
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -242,6 +267,8 @@ def main():
         return 0
     ctx = VMC(L, w.J1, w.J2, C, D, prec)
     ctx.set_params(torch.tensor(theta, device="cuda"))
+    tiles = ctx.autotune(L, probe_B=512)           # project autotuner: plain and light-cone tiles
+    cone_tiles = ctx.get_cone_tiles() if ctx.light_cone_active else None
     s_dev = torch.tensor(sig, device="cuda")
     eloc = torch.empty(B, dtype=torch.float64, device="cuda")
     nnb = None
@@ -250,10 +277,16 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    # exact neighbour counts for the algorithmic FLOPs of the E_loc launch
+    # exact neighbour counts for the algorithmic FLOPs of the E_loc launches:
+    # the parents' full forwards (parent pass) and the neighbours' light cones
     _, nnb = ctx.local_energy(s_dev)
     n_configs = int(B + nnb.sum().item())
-    flops_eloc = n_configs * f_fwd(L, C, D)
+    cone = ctx.light_cone_active
+    a1, a2 = antiparallel_counts(sig)
+    assert int(a1.sum() + a2.sum()) == n_configs - B
+    flops_parent = B * f_fwd(L, C, D)
+    flops_nbr = cone_flops(L, C, D, float(a1.sum()), float(a2.sum())) if cone else (n_configs - B) * f_fwd(L, C, D)
+    flops_eloc = flops_parent + flops_nbr
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
@@ -279,6 +312,7 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     times, launches = [], 0
+    ctx.set_launch_timing(True)            # an event pair around each tensor-core launch
     barrier()
     torch.cuda.synchronize()
     for _ in range(args.steps):
@@ -287,6 +321,11 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
+    kt = ctx.launch_timings()
+    ctx.set_launch_timing(False)
+    k_ms = {}
+    for name, ms in kt:
+        k_ms.setdefault(name, []).append(ms)
     step_ms = [a.elapsed_time(d) for a, b, c, d in times]
     eloc_ms = [a.elapsed_time(b) for a, b, c, d in times]
     od_ms = [b.elapsed_time(c) for a, b, c, d in times]
@@ -317,14 +356,32 @@ def main():
     e2e_value = world * B / (statistics.mean(e2e_ms) / 1e3)
 
     peak_t = peaks.get("bf16_tflops_sustained", FALLBACK_PEAKS["bf16_tflops_sustained"])
+    peak_b = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
     eloc_mean = statistics.mean(eloc_ms)
-    achieved = flops_eloc / (eloc_mean / 1e3) / 1e12
-    traffic = tc_traffic("tc_eloc_kernel<32,BF16,3> L=24", B) if w.name == "L24_bf16_sr" else None
+    if cone:
+        kname, kflops = "tc_eloc_kernel<light cone>", flops_nbr
+        kmean = statistics.mean(k_ms[kname])
+        parent_ms = statistics.mean(k_ms["tc_eloc_kernel<parent pass>"])
+        tkey = "tc_eloc_kernel<32,BF16> light cone L=24"
+    else:
+        kname, kflops = "tc_eloc_kernel", flops_eloc
+        kmean = statistics.mean(k_ms[kname])
+        parent_ms = None
+        tkey = "tc_eloc_kernel<32,BF16,3> L=24"
+    achieved = kflops / (kmean / 1e3) / 1e12
+    traffic = tc_traffic(tkey, B) if w.name == "L24_bf16_sr" else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_t, "unit": "TFLOP/s",
-                "frac": achieved / peak_t, "traffic": traffic, "kernel": "tc_eloc_kernel<32>",
-                "peak_source": f"{peak_src} bf16_tflops_sustained",
-                "algorithmic_flops_per_launch": flops_eloc, "configs_per_launch": n_configs,
-                "launch_ms": eloc_mean}
+                "frac": achieved / peak_t, "frac_of_burst_peak": achieved / peak_b, "traffic": traffic,
+                "kernel": kname, "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "algorithmic_flops_per_launch": kflops,
+                "flops_rule": ("exact light cone of each exchange neighbour ((2l+4)(2l+3) cells per layer "
+                               "for J1, (2l+4)^2 for J2, capped at L)" if cone else
+                               "full forward of every configuration"),
+                "configs_per_launch": n_configs - B if cone else n_configs, "launch_ms": kmean,
+                "timing": "CUDA events around each launch on its stream, mean over the timed steps"}
+    eloc_info = {"light_cone": bool(cone), "ms": eloc_mean, "parent_pass_ms": parent_ms,
+                 "algorithmic_flops": flops_eloc, "tflops": flops_eloc / (eloc_mean / 1e3) / 1e12,
+                 "full_forward_flops": n_configs * f_fwd(L, C, D)}
     sr_mean = statistics.mean(sr_ms)
     hbm = peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])
     sr_bytes = (w.cg_iters + 1) * B * ctx.n * 4
@@ -338,9 +395,10 @@ def main():
             "config": {"workload": w.name, "L": L, "C": C, "D": D, "batch": B, "params": ctx.n,
                        "neighbours_per_sample": (n_configs - B) / B, "sr_shift": w.shift,
                        "cg_iters": w.cg_iters, "parallelism": f"replicas x{world}",
+                       "tiles": tiles, "light_cone_tiles": cone_tiles,
                        "l2": "flushed before each step (256 MiB write outside the step's events)"},
             "breakdown_ms": {"eloc": eloc_mean, "log_derivs": statistics.mean(od_ms), "sr_solve": sr_mean},
-            "roofline": roofline, "roofline_sr": roofline_sr,
+            "roofline": roofline, "roofline_sr": roofline_sr, "eloc": eloc_info,
             "e2e": {"value": e2e_value, "unit": "samples/s", "h2d_bytes_per_step": int(sig_host.numel()),
                     "d2h_bytes_per_step": int(8 * B + 8 * ctx.n)},
             "gpu_launches": int(launches), "clocks": clk}
@@ -395,6 +453,8 @@ def side_measurements(torch, VMC, ev, stream, parts=SIDE_PARTS):
             sig, theta = inputs.workload_inputs(w, batch=B)
             ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, prec)
             ctx.set_params(torch.tensor(theta, device="cuda"))
+            if prec != "fp32":
+                ctx.autotune(w.L, probe_B=512)
             s = torch.tensor(sig, device="cuda")
             e = torch.empty(B, dtype=torch.float64, device="cuda")
             O = torch.empty(B, ctx.n, dtype=torch.float32, device="cuda")
@@ -414,9 +474,21 @@ def side_measurements(torch, VMC, ev, stream, parts=SIDE_PARTS):
                 ts.append((a.elapsed_time(b), b.elapsed_time(c)))
             te = min(t[0] for t in ts)
             to = min(t[1] for t in ts)
-            out[f"L{w.L}_{prec}"] = {"samples_per_s": B / ((te + to) / 1e3), "batch": B,
-                                     "eloc_ms": te, "log_derivs_ms": to,
-                                     "eloc_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (te / 1e3) / 1e12}
+            row = {"samples_per_s": B / ((te + to) / 1e3), "batch": B, "eloc_ms": te, "log_derivs_ms": to,
+                   "light_cone": bool(prec != "fp32" and ctx.light_cone_active),
+                   "eloc_full_forward_tflops": ncfg * f_fwd(w.L, w.C, w.D) / (te / 1e3) / 1e12}
+            if row["light_cone"]:
+                # the same call with every neighbour evaluated by a full forward
+                ctx.set_light_cone(False)
+                ctx.local_energy(s, out=e, n_nbr=False)
+                a, b = ev(), ev()
+                a.record(stream)
+                ctx.local_energy(s, out=e, n_nbr=False)
+                b.record(stream)
+                torch.cuda.synchronize()
+                row["eloc_plain_ms"] = a.elapsed_time(b)
+                ctx.set_light_cone(True)
+            out[f"L{w.L}_{prec}"] = row
             ctx.close()
             del O
             torch.cuda.empty_cache()

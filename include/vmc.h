@@ -283,6 +283,18 @@ int vmc_set_wait_budget(vmc_ctx *ctx, int64_t ns);
 int vmc_set_light_cone(vmc_ctx *ctx, int enable);
 int vmc_light_cone_active(const vmc_ctx *ctx, int *active);
 
+/* Launch timing of the tensor-core kernels, for measuring a kernel inside
+ * a public call: while enabled, every tensor-core launch is bracketed by a
+ * pair of CUDA events recorded on its stream.  vmc_set_launch_timing(ctx, 1)
+ * enables it and forgets earlier records; vmc_launch_timings synchronises
+ * on the recorded events and writes up to `max` durations (ms) in launch
+ * order, *count = the number recorded; vmc_launch_timing_name gives the
+ * kernel of record i (NULL beyond the count).  Host-side bookkeeping only
+ * (events are created on first use); not for use under stream capture. */
+int vmc_set_launch_timing(vmc_ctx *ctx, int enable);
+int vmc_launch_timings(vmc_ctx *ctx, int max, double *ms, int *count);
+const char *vmc_launch_timing_name(const vmc_ctx *ctx, int i);
+
 /* Launch one wait on an mbarrier that nothing arrives on, with the given
  * budget; the wait must give up and report VMC_ERR_TIMEOUT through
  * vmc_sync_status.  Exercises the timeout path without faulting the GPU. */
@@ -294,6 +306,16 @@ int vmc_debug_wait_timeout(vmc_ctx *ctx, int64_t budget_ns, void *stream);
 int vmc_set_tiles(vmc_ctx *ctx, int L, const vmc_tiles *tiles);
 int vmc_get_tiles(const vmc_ctx *ctx, int L, vmc_tiles *tiles);
 int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream);
+
+/* Tile choice of the light-cone pass (vmc_set_light_cone) for the
+ * context's lattice side: slabs (1 or 2), slab_configs = neighbour windows
+ * per slab, lane_cells = P; 0 fields are left to the cost model.  Set
+ * returns VMC_ERR_UNSUPPORTED (and keeps the previous choice) when no plan
+ * fits; get reports the plan in use (VMC_ERR_UNSUPPORTED where the light
+ * cone does not apply).  vmc_autotune(ctx, ctx's L, ...) also times the
+ * best-modelled light-cone plans and keeps the fastest. */
+int vmc_set_cone_tiles(vmc_ctx *ctx, const vmc_tiles *tiles);
+int vmc_get_cone_tiles(const vmc_ctx *ctx, vmc_tiles *tiles);
 
 /* Issue-rate probe of the tensor cores: `ctas` CTAs each issue `count`
  * back-to-back 128 x N x 16 BF16 UMMAs (N multiple of 16, <= 256);

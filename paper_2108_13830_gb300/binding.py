@@ -64,6 +64,11 @@ _SIGS = {
     "vmc_sync_status": (_I, [_P, _P, ct.POINTER(_I64)]),
     "vmc_set_wait_budget": (_I, [_P, _I64]),
     "vmc_set_light_cone": (_I, [_P, _I]),
+    "vmc_set_cone_tiles": (_I, [_P, _P]),
+    "vmc_get_cone_tiles": (_I, [_P, _P]),
+    "vmc_set_launch_timing": (_I, [_P, _I]),
+    "vmc_launch_timings": (_I, [_P, _I, _P, _P]),
+    "vmc_launch_timing_name": (ct.c_char_p, [_P, _I]),
     "vmc_light_cone_active": (_I, [_P, _P]),
     "vmc_debug_wait_timeout": (_I, [_P, _I64, _P]),
     "vmc_set_tiles": (_I, [_P, _I, ct.POINTER(vmc_tiles)]),
@@ -296,6 +301,19 @@ class VMC:
         self._check(lib().vmc_light_cone_active(self._h, ct.byref(a)))
         return bool(a.value)
 
+    def set_launch_timing(self, enable):
+        self._check(lib().vmc_set_launch_timing(self._h, 1 if enable else 0))
+
+    def launch_timings(self):
+        """[(kernel name, ms)] of the tensor-core launches recorded since
+        set_launch_timing(True)."""
+        cnt = ct.c_int(0)
+        self._check(lib().vmc_launch_timings(self._h, 0, None, ct.byref(cnt)))
+        n = cnt.value
+        ms = (ct.c_double * max(n, 1))()
+        self._check(lib().vmc_launch_timings(self._h, n, ms, ct.byref(cnt)))
+        return [(lib().vmc_launch_timing_name(self._h, i).decode(), ms[i]) for i in range(n)]
+
     def debug_wait_timeout(self, budget_ns):
         self._check(lib().vmc_debug_wait_timeout(self._h, int(budget_ns), _stream()))
 
@@ -308,6 +326,15 @@ class VMC:
         self._check(lib().vmc_get_tiles(self._h, L, ct.byref(t)))
         return {"slab_configs": t.slab_configs, "slabs": t.slabs, "ctas_per_sm": t.ctas_per_sm,
                 "lane_cells": t.lane_cells}
+
+    def set_cone_tiles(self, slab_configs=0, slabs=0, lane_cells=0):
+        t = vmc_tiles(slab_configs, slabs, 0, lane_cells)
+        self._check(lib().vmc_set_cone_tiles(self._h, ct.byref(t)))
+
+    def get_cone_tiles(self):
+        t = vmc_tiles()
+        self._check(lib().vmc_get_cone_tiles(self._h, ct.byref(t)))
+        return {"slab_configs": t.slab_configs, "slabs": t.slabs, "lane_cells": t.lane_cells}
 
     def autotune(self, L, probe_B=512):
         self._check(lib().vmc_autotune(self._h, L, int(probe_B), _stream()))

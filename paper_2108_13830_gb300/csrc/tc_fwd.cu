@@ -165,19 +165,17 @@ static LayerGeo cone_layer(int L, int l, int G, int P, int *rows)
 }
 
 // Modelled cycles of one neighbour through every layer with G windows per
-// slab: the MMA cost of each layer's tiles plus a fixed hand-off per
-// slab-layer, shared by the G windows.
+// slab: the MMA cost of each layer's tiles plus a hand-off per slab-layer
+// (the last tile's epilogue and the barrier), shared by the G windows.  With
+// one slab nothing hides the hand-off; with two the other slab's MMAs do.
 static double cone_cost(int C, int L, int D, int G, int P, int S)
 {
     double cyc = 0;
-    int tiles = 0;
     for (int l = 0; l <= D; ++l) {
         int rows;
         const LayerGeo g = cone_layer(L, l, G, P, &rows);
-        cyc += g.T * (l == 0 ? P * mma_cycles(C) : tile_cycles(C, P)) + 300.0;
-        tiles += g.T;
+        cyc += g.T * (l == 0 ? P * mma_cycles(C) : tile_cycles(C, P)) + (S == 1 ? 1800.0 : 300.0);
     }
-    if (S == 1) cyc *= 1.0 + 0.5 * (D + 1) / tiles;   // one slab: the layer hand-off is not overlapped
     return cyc / G;
 }
 
@@ -189,11 +187,16 @@ bool cone_applies_impl(const vmc_ctx *ctx)
     return vmc_is_tc(ctx->arch.precision) && L >= 6 && cone_w(L, D) == L;
 }
 
-static int make_cone_plan(const vmc_ctx *ctx, Plan *pl)
+// every (slabs, lane cells, windows per slab) of the light-cone pass that
+// fits shared memory, with its modelled cost
+struct ConeCand {
+    int S, P, G;
+    double score;
+};
+
+static void cone_cands(const vmc_ctx *ctx, std::vector<ConeCand> &out)
 {
     const int C = ctx->arch.channels, D = ctx->arch.n_layers_cc, L = ctx->L;
-    double best = 1e300;
-    int bS = 0, bG = 0, bP = 0;
     for (int S = 1; S <= 2; ++S) {
         const uint32_t buf = buf_bytes(C, S, L, D);
         for (int P = 1; P <= MAX_P; ++P) {
@@ -206,6 +209,33 @@ static int make_cone_plan(const vmc_ctx *ctx, Plan *pl)
                     rows_max = std::max(rows_max, rows);
                 }
                 if ((size_t)rows_max * P * C * 2 > buf) break;
+                out.push_back(ConeCand{S, P, G, cone_cost(C, L, D, G, P, S)});
+            }
+        }
+    }
+}
+
+static int make_cone_plan(const vmc_ctx *ctx, Plan *pl)
+{
+    const int C = ctx->arch.channels, D = ctx->arch.n_layers_cc, L = ctx->L;
+    const TileChoice &tc = ctx->cone_tiles;
+    double best = 1e300;
+    int bS = 0, bG = 0, bP = 0;
+    for (int S = 1; S <= 2; ++S) {
+        if (tc.slabs && S != tc.slabs) continue;
+        const uint32_t buf = buf_bytes(C, S, L, D);
+        for (int P = 1; P <= MAX_P; ++P) {
+            if (!p_allowed(C, P)) continue;
+            if (tc.lane_cells && P != tc.lane_cells) continue;
+            for (int G = 1; G <= MAX_SLOTS; ++G) {
+                int rows_max = 0;
+                for (int l = 0; l <= D; ++l) {
+                    int rows;
+                    cone_layer(L, l, G, P, &rows);
+                    rows_max = std::max(rows_max, rows);
+                }
+                if ((size_t)rows_max * P * C * 2 > buf) break;
+                if (tc.slab_configs && G != tc.slab_configs) continue;
                 const double sc = cone_cost(C, L, D, G, P, S);
                 if (sc < best - 1e-9) { best = sc; bS = S; bG = G; bP = P; }
             }
@@ -369,6 +399,19 @@ int vmc_tc_default_tiles(const vmc_ctx *ctx, int L, TileChoice *t)
 
 bool vmc_tc_cone_applies(const vmc_ctx *ctx) { return tc::cone_applies_impl(ctx); }
 
+int vmc_tc_cone_default_tiles(const vmc_ctx *ctx, TileChoice *t)
+{
+    if (!tc::cone_applies_impl(ctx)) return VMC_ERR_UNSUPPORTED;
+    tc::Plan pl;
+    const int rc = tc::make_cone_plan(ctx, &pl);
+    if (rc) return rc;
+    t->slab_configs = pl.geo[ctx->L >> 1].G;
+    t->slabs = pl.S;
+    t->ctas_per_sm = 1;
+    t->lane_cells = pl.P;
+    return VMC_OK;
+}
+
 // Local energy with light-cone neighbours (uniform L): per chunk of parents,
 // a parent pass (log|psi_CNN| and every layer's activations to the store),
 // then the neighbour pass, which recomputes only each neighbour's cone and
@@ -513,6 +556,37 @@ extern "C" int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream)
     }
     ctx->L = saved_L;
     ctx->tiles[L] = best;
+    // the light-cone pass (parent pass + neighbour pass, timed together) for
+    // the context's own lattice side
+    if (rc == VMC_OK && L == ctx->L && ctx->light_cone && tc::cone_applies_impl(ctx)) {
+        std::vector<tc::ConeCand> cc;
+        tc::cone_cands(ctx, cc);
+        std::stable_sort(cc.begin(), cc.end(),
+                         [](const tc::ConeCand &a, const tc::ConeCand &b) { return a.score < b.score; });
+        if (cc.size() > 8) cc.resize(8);
+        const TileChoice saved_c = ctx->cone_tiles;
+        TileChoice best_c = saved_c;
+        float best_c_ms = 1e30f;
+        for (size_t ci = 0; ci < cc.size() && rc == VMC_OK; ++ci) {
+            TileChoice t;
+            t.slabs = cc[ci].S;
+            t.slab_configs = cc[ci].G;
+            t.lane_cells = cc[ci].P;
+            t.ctas_per_sm = 1;
+            ctx->cone_tiles = t;
+            float ms = 0.f, best_rep = 1e30f;
+            for (int rep = 0; rep < 3 && rc == VMC_OK; ++rep) {
+                cudaEventRecord(e0, st);
+                rc = tc_eloc_cone(ctx, cfg, probe_B, out, nullptr, st);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) best_rep = std::min(best_rep, ms);
+            }
+            if (rc == VMC_OK && best_rep < best_c_ms) { best_c_ms = best_rep; best_c = t; }
+        }
+        ctx->cone_tiles = best_c;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(st);

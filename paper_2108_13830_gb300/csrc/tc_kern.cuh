@@ -1296,7 +1296,10 @@ static int launch_nm(vmc_ctx *ctx, const Plan &pl, const Params &p, cudaStream_t
     if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "counter reset");
     int grid = ctx->sm_count;
     if ((int64_t)grid > p.B) grid = (int)p.B;
+    static const char *names[3] = {"tc_eloc_kernel", "tc_eloc_kernel<parent pass>", "tc_eloc_kernel<light cone>"};
+    if (cudaEvent_t ev = vmc_timing_event(ctx, true, names[VAR])) cudaEventRecord(ev, st);
     kfn<<<grid, NTHREADS, pl.smem, st>>>(p);
+    if (cudaEvent_t ev = vmc_timing_event(ctx, false, nullptr)) cudaEventRecord(ev, st);
     ctx->launches += 1;
     return vmc_cuda_check(ctx, cudaGetLastError(), "tc_eloc launch");
 }

@@ -57,6 +57,24 @@ static bool arch_ok(int L, const vmc_arch *a, char *why, size_t nw)
     return true;
 }
 
+cudaEvent_t vmc_timing_event(vmc_ctx *ctx, bool start, const char *name)
+{
+    if (!ctx->timing) return nullptr;
+    const size_t i = 2 * ctx->tn + (start ? 0 : 1);
+    if (i >= ctx->tev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->tev.push_back(e);
+    }
+    if (start) {
+        if (ctx->tname.size() <= ctx->tn) ctx->tname.resize(ctx->tn + 1);
+        ctx->tname[ctx->tn] = name ? name : "";
+    } else {
+        ctx->tn += 1;
+    }
+    return ctx->tev[i];
+}
+
 extern "C" {
 
 int vmc_create(int L, double J1, double J2, const vmc_arch *arch, vmc_ctx **out)
@@ -109,6 +127,7 @@ void vmc_destroy(vmc_ctx *ctx)
     cudaFree(ctx->bias); cudaFree(ctx->bias32); cudaFree(ctx->wimg);
     cudaFree(ctx->status); cudaFree(ctx->counter);
     cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws); cudaFree(ctx->sym_ws); cudaFree(ctx->sym_cnt); cudaFree(ctx->cone_ws);
+    for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -316,6 +335,36 @@ int vmc_set_wait_budget(vmc_ctx *ctx, int64_t ns)
     return VMC_OK;
 }
 
+int vmc_set_launch_timing(vmc_ctx *ctx, int enable)
+{
+    if (!ctx || (enable != 0 && enable != 1)) return VMC_ERR_ARG;
+    ctx->timing = enable;
+    ctx->tn = 0;
+    return VMC_OK;
+}
+
+int vmc_launch_timings(vmc_ctx *ctx, int max, double *ms, int *count)
+{
+    if (!ctx || !count || max < 0 || (max > 0 && !ms)) return VMC_ERR_ARG;
+    const int n = (int)ctx->tn;
+    *count = n;
+    for (int i = 0; i < n && i < max; ++i) {
+        cudaError_t e = cudaEventSynchronize(ctx->tev[2 * i + 1]);
+        if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "timing event");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, ctx->tev[2 * i], ctx->tev[2 * i + 1]);
+        if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "timing elapsed");
+        ms[i] = t;
+    }
+    return VMC_OK;
+}
+
+const char *vmc_launch_timing_name(const vmc_ctx *ctx, int i)
+{
+    if (!ctx || i < 0 || (size_t)i >= ctx->tn) return nullptr;
+    return ctx->tname[i].c_str();
+}
+
 int vmc_set_light_cone(vmc_ctx *ctx, int enable)
 {
     if (!ctx || (enable != 0 && enable != 1)) return VMC_ERR_ARG;
@@ -365,6 +414,40 @@ int vmc_get_tiles(const vmc_ctx *ctx, int L, vmc_tiles *tiles)
     tiles->slabs = t.slabs ? t.slabs : d.slabs;
     tiles->ctas_per_sm = t.ctas_per_sm ? t.ctas_per_sm : d.ctas_per_sm;
     tiles->lane_cells = t.lane_cells ? t.lane_cells : d.lane_cells;
+    return VMC_OK;
+}
+
+int vmc_set_cone_tiles(vmc_ctx *ctx, const vmc_tiles *tiles)
+{
+    if (!ctx || !tiles) return VMC_ERR_ARG;
+    TileChoice t;
+    t.slab_configs = tiles->slab_configs;
+    t.slabs = tiles->slabs;
+    t.ctas_per_sm = tiles->ctas_per_sm;
+    t.lane_cells = tiles->lane_cells;
+    if (t.slabs < 0 || t.slabs > 2 || t.slab_configs < 0 || t.slab_configs > 16 || t.ctas_per_sm < 0 ||
+        t.ctas_per_sm > 1 || t.lane_cells < 0 || t.lane_cells > 8)
+        return vmc_fail(ctx, VMC_ERR_ARG, "light-cone tile choice out of range");
+    const TileChoice saved = ctx->cone_tiles;
+    ctx->cone_tiles = t;
+    TileChoice d;
+    if (vmc_tc_cone_applies(ctx) && vmc_tc_cone_default_tiles(ctx, &d) != VMC_OK) {
+        ctx->cone_tiles = saved;
+        return vmc_fail(ctx, VMC_ERR_UNSUPPORTED, "no light-cone plan with these tiles");
+    }
+    return VMC_OK;
+}
+
+int vmc_get_cone_tiles(const vmc_ctx *ctx, vmc_tiles *tiles)
+{
+    if (!ctx || !tiles) return VMC_ERR_ARG;
+    TileChoice d;
+    const int rc = vmc_tc_cone_default_tiles(ctx, &d);
+    if (rc) return rc;
+    tiles->slab_configs = d.slab_configs;
+    tiles->slabs = d.slabs;
+    tiles->ctas_per_sm = d.ctas_per_sm;
+    tiles->lane_cells = d.lane_cells;
     return VMC_OK;
 }
 

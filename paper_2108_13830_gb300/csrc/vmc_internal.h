@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <string>
 #include <map>
+#include <vector>
 
 #include "../../include/vmc.h"
 
@@ -74,6 +75,14 @@ struct vmc_ctx {
     void *cone_ws = nullptr;     // light-cone E_loc: parent activations, log|psi| and signs
     size_t cone_ws_bytes = 0;
     int light_cone = 1;          // evaluate E_loc neighbours incrementally where it applies
+    TileChoice cone_tiles;       // light-cone pass tile choice (0 fields: cost model)
+
+    // launch timing of the tensor-core kernels (vmc_set_launch_timing):
+    // an event pair around each launch on its stream, with the kernel's name
+    int timing = 0;
+    std::vector<cudaEvent_t> tev;
+    std::vector<std::string> tname;
+    size_t tn = 0;               // pairs recorded since timing was (re)enabled
 
     int64_t wait_budget_ns = 2000000000LL;
     std::map<int, TileChoice> tiles;
@@ -96,6 +105,9 @@ struct vmc_ctx {
 int vmc_fail(vmc_ctx *ctx, int code, const char *fmt, ...);
 int vmc_cuda_check(vmc_ctx *ctx, cudaError_t e, const char *what);
 int vmc_ensure_ws(vmc_ctx *ctx, void **buf, size_t *cur, size_t need);
+// launch timing: the event to record before (start = true) or after a
+// kernel launch named `name` (nullptr when timing is off)
+cudaEvent_t vmc_timing_event(vmc_ctx *ctx, bool start, const char *name);
 
 // parameter preparation (prep.cu)
 int vmc_prepare_params(vmc_ctx *ctx, const void *theta, int dtype, cudaStream_t s);
@@ -115,6 +127,7 @@ int vmc_tc_eloc(vmc_ctx *ctx, int mode, const int8_t *sigma, const int64_t *offs
                 int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr, cudaStream_t s);
 int vmc_tc_default_tiles(const vmc_ctx *ctx, int L, TileChoice *t);
 bool vmc_tc_cone_applies(const vmc_ctx *ctx);
+int vmc_tc_cone_default_tiles(const vmc_ctx *ctx, TileChoice *t);
 int vmc_tc_debug_timeout(vmc_ctx *ctx, int64_t budget_ns, cudaStream_t s);
 
 // Metropolis sampling (mcmc.cu)

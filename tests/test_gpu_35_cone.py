@@ -147,3 +147,37 @@ def test_cone_parent_chunks():
     assert r1 == r0 == (VMC_OK, 0)
     np.testing.assert_array_equal(n1, n0)
     np.testing.assert_array_equal(e1, e0)
+
+
+@pytest.mark.parametrize("L,C,D,prec", [(16, 32, 8, "bf16"), (10, 16, 6, "fp16")])
+def test_cone_tile_choices_and_autotune(L, C, D, prec):
+    """Every explicit light-cone tile choice that fits, and the autotuned
+    one, give the plain evaluation's results bit for bit."""
+    w = inputs.Workload(f"conet{L}", L, C, D, prec, 64, index=80 + L)
+    sig, theta = inputs.workload_inputs(w)
+    v = make_ctx(w, theta=theta)
+    s = to_dev(sig)
+    v.set_light_cone(False)
+    e0, _ = v.local_energy(s)
+    v.set_light_cone(True)
+    e0 = e0.cpu().numpy()
+    tried = 0
+    for S in (1, 2):
+        for P in (2, 3, 4):
+            for G in (1, 2, 3):
+                try:
+                    v.set_cone_tiles(slab_configs=G, slabs=S, lane_cells=P)
+                except Exception:
+                    continue
+                got = v.get_cone_tiles()
+                assert (got["slabs"], got["lane_cells"], got["slab_configs"]) == (S, P, G)
+                e1, _ = v.local_energy(s)
+                assert v.sync_status()[0] == VMC_OK
+                np.testing.assert_array_equal(e1.cpu().numpy(), e0)
+                tried += 1
+    assert tried >= 4
+    v.set_cone_tiles()
+    v.autotune(L, probe_B=256)
+    e2, _ = v.local_energy(s)
+    assert v.sync_status()[0] == VMC_OK
+    np.testing.assert_array_equal(e2.cpu().numpy(), e0)
