@@ -64,6 +64,7 @@ _SIGS = {
     "vmc_sync_status": (_I, [_P, _P, ct.POINTER(_I64)]),
     "vmc_set_wait_budget": (_I, [_P, _I64]),
     "vmc_set_light_cone": (_I, [_P, _I]),
+    "vmc_set_sr_fused": (_I, [_P, _I]),
     "vmc_set_cone_tiles": (_I, [_P, _P]),
     "vmc_get_cone_tiles": (_I, [_P, _P]),
     "vmc_set_launch_timing": (_I, [_P, _I]),
@@ -291,6 +292,9 @@ class VMC:
 
     def set_wait_budget(self, ns):
         self._check(lib().vmc_set_wait_budget(self._h, int(ns)))
+
+    def set_sr_fused(self, enable):
+        self._check(lib().vmc_set_sr_fused(self._h, 1 if enable else 0))
 
     def set_light_cone(self, enable):
         self._check(lib().vmc_set_light_cone(self._h, 1 if enable else 0))

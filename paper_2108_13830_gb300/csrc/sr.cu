@@ -12,6 +12,7 @@
 // the same quantity (Obar . v = tbar).
 #include <algorithm>
 #include "vmc_internal.h"
+#include "tc_ptx.cuh"
 
 namespace vmc {
 
@@ -239,6 +240,251 @@ __global__ void __launch_bounds__(256) rowdot_blk_kernel(const float *__restrict
     }
 }
 
+// ---------------------------------------------------------------- fused S v
+//
+// u = (1/m) O^T (t - tbar) with t = O v in ONE pass over O.  A cooperative
+// launch of nC CTAs; CTA c owns the columns [c W, c W + W) and walks the rows
+// in blocks of SV_R, each block's rows streamed by bulk copies into a ring of
+// SV_STAGES shared-memory stages.  For block i a CTA forms the dots of its
+// column slice with the block's rows (one warp per row), publishes them and
+// counts itself in; one block later, once every CTA has counted in, it adds
+// the nC partials of each row in a fixed order (the same sum in every CTA),
+// centres them with tbar = Obar . v (published the same way at the start),
+// and accumulates sum_b O_bk d_b for its columns from the stage still in
+// shared memory.  Every element of O is read once from HBM; all products and
+// sums are double-float as in the two-pass kernels.  Each wait is bounded by
+// a time budget and reports VMC_ERR_TIMEOUT.
+
+constexpr int SV_R = 8;           // rows per block (two warps per row in the dot phase)
+constexpr int SV_STAGES = 10;     // shared-memory stages of SV_R rows
+constexpr int SV_LAG = 5;         // blocks between publishing a block's dots and using them
+constexpr int SV_THREADS = 512;
+constexpr int SV_WARPS = SV_THREADS / 32;
+constexpr int SV_MAXW = 2 * SV_THREADS;   // columns per CTA: two per thread in the column phase
+static_assert(SV_WARPS == 2 * SV_R, "two warps per row");
+static_assert(SV_STAGES >= SV_LAG + 2, "the stages hold the lagging blocks plus loads ahead");
+
+struct SvParams {
+    const float *O;
+    int64_t m, n;
+    int W, nblk;
+    const float *vh, *vl;      // split v, [n]
+    const double *Obar;        // [n]
+    double inv_m;
+    float2 *part;              // [nblk][nC][SV_R] partial dots
+    float2 *bar_part;          // [nC] partial Obar . v
+    int *cnt;                  // [nblk + 1] arrivals (block i; tbar last), zero at launch
+    double *u;                 // [n]
+    DevStatus *status;
+    long long budget_ns;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// wait until *p >= target (every CTA counted in), bounded by the budget
+__device__ bool wait_count(const int *p, int target, long long budget_ns, DevStatus *st)
+{
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (ld_acquire_gpu(p) >= target) return true;
+        if ((it & 63u) == 63u) {
+            const uint64_t now = global_timer_ns();
+            if (t0 == 0) t0 = now;
+            else if ((long long)(now - t0) > budget_ns) {
+                atomicOr(&st->flags, VMC_STATUS_TIMEOUT);
+                st->timeout_site = 40;
+                return false;
+            }
+        }
+        __nanosleep(32);
+    }
+}
+
+__device__ __forceinline__ DF warp_df_sum(DF a)
+{
+    for (int off = 16; off > 0; off >>= 1) {
+        const DF o = df_shfl_xor(a, off);
+        df_add_df(a, o);
+    }
+    return a;
+}
+
+__global__ void __launch_bounds__(SV_THREADS, 1) sv_fused_kernel(const __grid_constant__ SvParams q)
+{
+    extern __shared__ __align__(128) uint8_t sv_smem[];
+    __shared__ uint64_t full[SV_STAGES];
+    __shared__ float dh[SV_R], dl[SV_R], th[SV_R], tl[SV_R];
+    __shared__ float red_h[SV_WARPS], red_l[SV_WARPS];
+    __shared__ float tbar_h, tbar_l;
+    __shared__ double dsum_s;
+    __shared__ int abort_flag, site_dummy;
+    const int nC = gridDim.x, c = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int W = q.W;
+    const int64_t k0 = (int64_t)c * W;
+    const int Wc = (int)min((int64_t)W, q.n - k0);
+    float *stage = reinterpret_cast<float *>(sv_smem);
+    float *svh = stage + (size_t)SV_STAGES * SV_R * W;
+    float *svl = svh + W;
+    int issued = 0, consumed = 0;
+    auto rows_of = [&](int i) { return (int)min((int64_t)SV_R, q.m - (int64_t)i * SV_R); };
+    auto issue = [&](int i) {
+        const int s = i % SV_STAGES, rows = rows_of(i);
+        const uint32_t bytes = (uint32_t)Wc * 4u;
+        mbar_expect_tx(&full[s], bytes * (uint32_t)rows);
+        for (int r = 0; r < rows; ++r)
+            bulk_g2s(stage + ((size_t)s * SV_R + r) * W, q.O + ((int64_t)i * SV_R + r) * q.n + k0, bytes, &full[s]);
+    };
+    if (tid == 0) {
+        for (int s = 0; s < SV_STAGES; ++s) mbar_init(&full[s], 1);
+        mbar_fence_init();
+        abort_flag = 0;
+    }
+    for (int k = tid; k < Wc; k += SV_THREADS) { svh[k] = q.vh[k0 + k]; svl[k] = q.vl[k0 + k]; }
+    __syncthreads();
+    if (tid == 0)
+        for (; issued < min(SV_STAGES, q.nblk); ++issued) issue(issued);
+    // partial tbar = sum over the slice of Obar_k v_k
+    {
+        DF a{0.f, 0.f};
+        for (int k = tid; k < Wc; k += SV_THREADS) {
+            float oh, ol;
+            split(q.Obar[k0 + k], oh, ol);
+            df_mac(a, oh, svh[k], svl[k]);
+            df_add(a, ol * svh[k]);
+        }
+        a = warp_df_sum(a);
+        if (lane == 0) { red_h[warp] = a.h; red_l[warp] = a.l; }
+        __syncthreads();
+        if (tid == 0) {
+            DF b{0.f, 0.f};
+            for (int w = 0; w < SV_WARPS; ++w) df_add_df(b, DF{red_h[w], red_l[w]});
+            q.bar_part[c] = make_float2(b.h, b.l);
+            __threadfence();
+            atomicAdd(&q.cnt[q.nblk], 1);
+        }
+        __syncthreads();
+    }
+    DF acc0{0.f, 0.f}, acc1{0.f, 0.f};
+    DF dsum{0.f, 0.f};   // thread 0: sum_b d_b
+    for (int i = 0; i < q.nblk + SV_LAG; ++i) {
+        if (i < q.nblk) {
+            // dot phase: block i, row warp / 2, half warp % 2 of the slice
+            const int s = i % SV_STAGES;
+            if (tid == 0) {
+                const bool ok = mbar_wait_bounded(&full[s], (uint32_t)((i / SV_STAGES) & 1), &abort_flag, q.budget_ns,
+                                                  &q.status->flags, &site_dummy, 41);
+                if (!ok) abort_flag = 1;
+            }
+            __syncthreads();
+            if (abort_flag) break;
+            consumed = i + 1;
+            const int rows = rows_of(i), r = warp >> 1, hf = warp & 1;
+            DF a{0.f, 0.f};
+            if (r < rows) {
+                const float *row = stage + ((size_t)s * SV_R + r) * W;
+                for (int k = (hf * 32 + lane) * 4; k < Wc; k += 256) {
+                    const float4 o = *reinterpret_cast<const float4 *>(row + k);
+                    const float4 h = *reinterpret_cast<const float4 *>(svh + k);
+                    const float4 l = *reinterpret_cast<const float4 *>(svl + k);
+                    df_mac(a, o.x, h.x, l.x);
+                    df_mac(a, o.y, h.y, l.y);
+                    df_mac(a, o.z, h.z, l.z);
+                    df_mac(a, o.w, h.w, l.w);
+                }
+                a = warp_df_sum(a);
+            }
+            if (lane == 0) { red_h[warp] = a.h; red_l[warp] = a.l; }
+            __syncthreads();
+            if (tid < rows) {
+                DF b{red_h[2 * tid], red_l[2 * tid]};
+                df_add_df(b, DF{red_h[2 * tid + 1], red_l[2 * tid + 1]});
+                q.part[((size_t)i * nC + c) * SV_R + tid] = make_float2(b.h, b.l);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(&q.cnt[i], 1);
+            }
+        }
+        const int j = i - SV_LAG;
+        if (j >= 0) {
+            if (tid == 0) {
+                bool ok = wait_count(&q.cnt[j], nC, q.budget_ns, q.status);
+                if (ok && j == 0) ok = wait_count(&q.cnt[q.nblk], nC, q.budget_ns, q.status);
+                if (!ok) abort_flag = 1;
+            }
+            __syncthreads();
+            if (abort_flag) break;
+            const int rows = rows_of(j);
+            // row sums of the nC partials (lane-strided, then a fixed shuffle tree)
+            if (warp < rows) {
+                DF a{0.f, 0.f};
+                for (int cc = lane; cc < nC; cc += 32) {
+                    const float2 v = __ldcg(q.part + ((size_t)j * nC + cc) * SV_R + warp);
+                    df_add_df(a, DF{v.x, v.y});
+                }
+                a = warp_df_sum(a);
+                if (lane == 0) { th[warp] = a.h; tl[warp] = a.l; }
+            }
+            if (j == 0 && warp == SV_WARPS - 1) {
+                DF a{0.f, 0.f};
+                for (int cc = lane; cc < nC; cc += 32) {
+                    const float2 v = __ldcg(q.bar_part + cc);
+                    df_add_df(a, DF{v.x, v.y});
+                }
+                a = warp_df_sum(a);
+                if (lane == 0) { tbar_h = a.h; tbar_l = a.l; }
+            }
+            __syncthreads();
+            if (tid < rows) {
+                // d_b = (t_b - tbar) / m, split for the column phase
+                DF t{th[tid], tl[tid]};
+                df_add_df(t, DF{-tbar_h, -tbar_l});
+                split(((double)t.h + (double)t.l) * q.inv_m, dh[tid], dl[tid]);
+            }
+            __syncthreads();
+            // the sum of the d_b used, the same in every CTA (see the end)
+            if (tid == 0)
+                for (int rr = 0; rr < rows; ++rr) { df_add(dsum, dh[rr]); df_add(dsum, dl[rr]); }
+            const float *st = stage + (size_t)(j % SV_STAGES) * SV_R * W;
+            for (int rr = 0; rr < rows; ++rr) {
+                const float hh = dh[rr], ll = dl[rr];
+                if (tid < Wc) df_mac(acc0, st[rr * W + tid], hh, ll);
+                if (tid + SV_THREADS < Wc) df_mac(acc1, st[rr * W + tid + SV_THREADS], hh, ll);
+            }
+            __syncthreads();   // stage j % SV_STAGES is free again
+            if (tid == 0 && issued < q.nblk) issue(issued++);
+        }
+    }
+    if (abort_flag) {
+        // a wait gave up: drain this CTA's bulk copies (bounded) before exiting
+        if (tid == 0) {
+            int dummy = 0;
+            for (int b = consumed; b < issued; ++b)
+                mbar_wait_bounded(&full[b % SV_STAGES], (uint32_t)((b / SV_STAGES) & 1), &dummy, q.budget_ns,
+                                  &q.status->flags, &site_dummy, 42);
+        }
+        __syncthreads();
+        return;
+    }
+    // tbar = Obar . v differs from the mean of the computed t_b by rounding,
+    // so sum_b d_b is not exactly 0, and on columns whose mean is large that
+    // leftover, times sum_b O_bk = m Obar_k, would dominate the error.
+    // Centring the d_b on their own mean instead (what the two-pass kernels
+    // do with t) subtracts Obar_k sum_b d_b.
+    if (tid == 0) dsum_s = (double)dsum.h + (double)dsum.l;
+    __syncthreads();
+    const double sd = dsum_s;
+    if (tid < Wc) q.u[k0 + tid] = ((double)acc0.h + (double)acc0.l) - q.Obar[k0 + tid] * sd;
+    if (tid + SV_THREADS < Wc)
+        q.u[k0 + tid + SV_THREADS] = ((double)acc1.h + (double)acc1.l) - q.Obar[k0 + tid + SV_THREADS] * sd;
+}
+
 // ---------------------------------------------------------------- CG
 
 // q = u + shift p; partial dot p.q per CTA
@@ -342,6 +588,8 @@ struct SrWs {
     double *r, *p, *q;     // [n]
     double *scal;          // scalars: 0 Ebar, 1 tbar, 2 gg, 3..4 rr[2], 5 resid
     double *pq_part, *rr_part, *gg_part;   // [NPART]
+    float2 *sv_part, *sv_bar;              // fused S v: [nblk][nC][SV_R], [nC]
+    int *sv_cnt;                           // [nblk + 1]
 };
 constexpr int NPART = 256;
 
@@ -350,12 +598,14 @@ static int64_t nchunks_for(int64_t m) { return m >= 1024 ? 16 : (m >= 64 ? 4 : 1
 static int sr_workspace(vmc_ctx *ctx, int64_t m, SrWs *w)
 {
     const int64_t n = ctx->n, nch = nchunks_for(m);
+    const int64_t nblk = (m + SV_R - 1) / SV_R, nC = std::max(ctx->sm_count, 1);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
-    size_t off[16], tot = 0;
+    size_t off[19], tot = 0;
     size_t sz[] = {n * 4, n * 4, (size_t)m * 4, (size_t)m * 4, (size_t)m * 8, (size_t)nch * n * 8, (size_t)nch * n * 8,
                    (size_t)n * 8, (size_t)n * 8, (size_t)n * 8, (size_t)n * 8, (size_t)n * 8, 64 * 8,
-                   NPART * 8, NPART * 8, NPART * 8};
-    for (int i = 0; i < 16; ++i) { off[i] = tot; tot += al(sz[i]); }
+                   NPART * 8, NPART * 8, NPART * 8,
+                   (size_t)nblk * nC * SV_R * 8, (size_t)nC * 8, (size_t)(nblk + 1) * 4};
+    for (int i = 0; i < 19; ++i) { off[i] = tot; tot += al(sz[i]); }
     int rc = vmc_ensure_ws(ctx, &ctx->sr_ws, &ctx->sr_ws_bytes, tot);
     if (rc) return rc;
     char *b = static_cast<char *>(ctx->sr_ws);
@@ -367,6 +617,7 @@ static int sr_workspace(vmc_ctx *ctx, int64_t m, SrWs *w)
     w->r = (double *)(b + off[9]); w->p = (double *)(b + off[10]); w->q = (double *)(b + off[11]);
     w->scal = (double *)(b + off[12]);
     w->pq_part = (double *)(b + off[13]); w->rr_part = (double *)(b + off[14]); w->gg_part = (double *)(b + off[15]);
+    w->sv_part = (float2 *)(b + off[16]); w->sv_bar = (float2 *)(b + off[17]); w->sv_cnt = (int *)(b + off[18]);
     return VMC_OK;
 }
 
@@ -388,6 +639,71 @@ static void launch_moments(vmc_ctx *ctx, const float *O, const double *E, int64_
     reduce_chunks_kernel<<<rg, 256, 0, s>>>(w.part1, (int)nch, n, 1.0 / (double)m, nullptr, 0.0, Obar);
     reduce_chunks_kernel<<<rg, 256, 0, s>>>(w.part2, (int)nch, n, 1.0 / (double)m, nullptr, 0.0, G);
     ctx->launches += 4;
+}
+
+// Geometry of the fused S v for O [m][n]: CTAs, columns per CTA (a multiple
+// of 4, at most two per thread) and dynamic shared memory; false where it
+// does not apply (unaligned rows, too many columns per CTA), and the
+// two-pass kernels run instead.
+struct SvPlan {
+    int nC, W, nblk;
+    size_t smem;
+};
+
+static bool sv_fused_plan(const vmc_ctx *ctx, const float *O, int64_t m, SvPlan *pl)
+{
+    const int64_t n = ctx->n;
+    if (!vec_ok(O, n) || m < 1 || ctx->sm_count < 1) return false;
+    int nc = (int)std::min<int64_t>(ctx->sm_count, (n + 127) / 128);
+    const int64_t n4 = n / 4;
+    const int W = (int)(4 * ((n4 + nc - 1) / nc));
+    nc = (int)((n + W - 1) / W);
+    if (W > SV_MAXW) return false;
+    pl->nC = nc;
+    pl->W = W;
+    pl->nblk = (int)((m + SV_R - 1) / SV_R);
+    pl->smem = (size_t)SV_STAGES * SV_R * W * 4 + 2 * (size_t)W * 4;
+    if (pl->smem > 220 * 1024) return false;
+    static int smem_set[64] = {0};
+    const int dev = ctx->device;
+    if (dev < 0 || dev >= 64 || smem_set[dev] < (int)pl->smem) {
+        if (cudaFuncSetAttribute(sv_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem) !=
+            cudaSuccess)
+            return false;
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sv_fused_kernel, SV_THREADS, pl->smem) !=
+                cudaSuccess || per_sm < 1)
+            return false;
+        if (dev >= 0 && dev < 64) smem_set[dev] = (int)pl->smem;
+    }
+    return true;
+}
+
+// u = (1/m) O^T (O v - tbar) into w.part2 (one chunk) with v split in
+// (vh, vl): a counter reset and one cooperative launch
+static int launch_sv_fused(vmc_ctx *ctx, const float *O, int64_t m, const double *Obar, const SrWs &w,
+                           const SvPlan &pl, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(w.sv_cnt, 0, (size_t)(pl.nblk + 1) * sizeof(int), s);
+    if (e != cudaSuccess) return vmc_cuda_check(ctx, e, "S v counters");
+    SvParams q;
+    q.O = O; q.m = m; q.n = ctx->n; q.W = pl.W; q.nblk = pl.nblk;
+    q.vh = w.vh; q.vl = w.vl; q.Obar = Obar; q.inv_m = 1.0 / (double)m;
+    q.part = w.sv_part; q.bar_part = w.sv_bar; q.cnt = w.sv_cnt; q.u = w.part2;
+    q.status = ctx->status; q.budget_ns = ctx->wait_budget_ns;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)pl.nC);
+    cfg.blockDim = dim3(SV_THREADS);
+    cfg.dynamicSmemBytes = pl.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;   // the CTAs wait on one another
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, sv_fused_kernel, q);
+    ctx->launches += 1;
+    return vmc_cuda_check(ctx, e, "fused S v launch");
 }
 
 // u-partials of S p: rowdot, centre, column dots (p already split into vh/vl)
@@ -424,15 +740,24 @@ int vmc_sr_moments_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m
 int vmc_sr_matvec_impl(vmc_ctx *ctx, const float *O, int64_t m, const double *Obar,
                        const double *v, double shift, double *out, cudaStream_t s)
 {
-    (void)Obar;   // Obar . v equals the mean of t = O v; see the file comment
+    // the two-pass kernels centre t with its own mean (Obar . v equals the
+    // mean of t = O v; see the file comment); the fused one uses Obar . v
     SrWs w;
     int rc = sr_workspace(ctx, m, &w);
     if (rc) return rc;
     const int64_t n = ctx->n, nch = nchunks_for(m);
     const int g = (int)std::min<int64_t>((n + 255) / 256, 4 * ctx->sm_count);
     split_kernel<<<g, 256, 0, s>>>(v, n, w.vh, w.vl);
-    launch_sv_partials(ctx, O, m, w, s);
-    reduce_chunks_kernel<<<g, 256, 0, s>>>(w.part2, (int)nch, n, 1.0, v, shift, out);
+    SvPlan pl;
+    int used = (int)nch;
+    if (ctx->sr_fused && Obar && sv_fused_plan(ctx, O, m, &pl)) {
+        rc = launch_sv_fused(ctx, O, m, Obar, w, pl, s);
+        if (rc) return rc;
+        used = 1;
+    } else {
+        launch_sv_partials(ctx, O, m, w, s);
+    }
+    reduce_chunks_kernel<<<g, 256, 0, s>>>(w.part2, used, n, 1.0, v, shift, out);
     ctx->launches += 2;
     return vmc_cuda_check(ctx, cudaGetLastError(), "sr matvec");
 }
@@ -472,11 +797,14 @@ static void record_cg(vmc_ctx *ctx, const float *O, int64_t m, double shift, int
     cg_init_kernel<<<np, 256, 0, s>>>(w.G, n, x, w.r, w.p, w.vh, w.vl, w.gg_part);
     finalize_scalar_kernel<<<1, 32, 0, s>>>(w.gg_part, np, gg, rr0);
     ctx->launches += 2;
+    SvPlan pl;
+    const bool fused = ctx->sr_fused && sv_fused_plan(ctx, O, m, &pl);
     for (int it = 0; it < iters; ++it) {
         double *rr_old = (it & 1) ? rr1 : rr0;
         double *rr_new = (it & 1) ? rr0 : rr1;
-        launch_sv_partials(ctx, O, m, w, s);
-        cg_q_kernel<<<np, 256, 0, s>>>(w.part2, (int)nch, n, shift, w.p, w.q, w.pq_part);
+        if (fused) launch_sv_fused(ctx, O, m, w.Obar, w, pl, s);
+        else launch_sv_partials(ctx, O, m, w, s);
+        cg_q_kernel<<<np, 256, 0, s>>>(w.part2, fused ? 1 : (int)nch, n, shift, w.p, w.q, w.pq_part);
         cg_update_kernel<<<np, 256, 0, s>>>(w.pq_part, np, rr_old, x, w.r, w.p, w.q, n, w.rr_part);
         cg_dir_kernel<<<np, 256, 0, s>>>(w.rr_part, np, rr_old, rr_new, w.r, w.p, n, w.vh, w.vl);
         ctx->launches += 3;
@@ -495,7 +823,7 @@ int vmc_sr_solve_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m, 
     rc = vmc_cuda_check(ctx, cudaGetLastError(), "sr moments");
     if (rc) return rc;
     const bool same = ctx->cg_exec && ctx->cg_key_ws == ctx->sr_ws && ctx->cg_key_O == O && ctx->cg_key_m == m && ctx->cg_key_iters == iters &&
-                      ctx->cg_key_shift == shift && ctx->cg_key_x == x;
+                      ctx->cg_key_shift == shift && ctx->cg_key_x == x && ctx->cg_key_fused == ctx->sr_fused;
     if (!same) {
         if (ctx->cg_exec) { cudaGraphExecDestroy(ctx->cg_exec); ctx->cg_exec = nullptr; }
         cudaStream_t cap;
@@ -514,6 +842,7 @@ int vmc_sr_solve_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m, 
         if (e != cudaSuccess) { ctx->cg_exec = nullptr; return vmc_cuda_check(ctx, e, "graph instantiate"); }
         ctx->cg_key_O = O; ctx->cg_key_m = m; ctx->cg_key_iters = iters; ctx->cg_key_shift = shift; ctx->cg_key_x = x;
         ctx->cg_key_ws = ctx->sr_ws;
+        ctx->cg_key_fused = ctx->sr_fused;
         ctx->cg_launches = ctx->launches - saved;
         ctx->launches = saved;
     }

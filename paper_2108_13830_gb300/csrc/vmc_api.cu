@@ -365,6 +365,13 @@ const char *vmc_launch_timing_name(const vmc_ctx *ctx, int i)
     return ctx->tname[i].c_str();
 }
 
+int vmc_set_sr_fused(vmc_ctx *ctx, int enable)
+{
+    if (!ctx || (enable != 0 && enable != 1)) return VMC_ERR_ARG;
+    ctx->sr_fused = enable;
+    return VMC_OK;
+}
+
 int vmc_set_light_cone(vmc_ctx *ctx, int enable)
 {
     if (!ctx || (enable != 0 && enable != 1)) return VMC_ERR_ARG;

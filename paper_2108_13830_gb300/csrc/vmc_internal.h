@@ -76,6 +76,7 @@ struct vmc_ctx {
     size_t cone_ws_bytes = 0;
     int light_cone = 1;          // evaluate E_loc neighbours incrementally where it applies
     TileChoice cone_tiles;       // light-cone pass tile choice (0 fields: cost model)
+    int sr_fused = 0;            // S v in one pass over O (off: two passes, faster; see vmc.h)
 
     // launch timing of the tensor-core kernels (vmc_set_launch_timing):
     // an event pair around each launch on its stream, with the kernel's name
@@ -95,6 +96,7 @@ struct vmc_ctx {
     double cg_key_shift = 0;
     void *cg_key_x = nullptr;
     void *cg_key_ws = nullptr;
+    int cg_key_fused = -1;
     int64_t cg_launches = 0;
 
     int64_t launches = 0;

@@ -112,3 +112,47 @@ def test_single_sample_gives_zero():
     E = inputs.synthetic_E(1, rng)
     x, res = v.sr_solve(to_dev(O), to_dev(E), 1e-4, 50)
     assert torch.count_nonzero(x).item() == 0 and res == 0.0
+
+
+@pytest.mark.parametrize("m,C,D", [(1, 4, 2), (17, 4, 2), (300, 16, 6), (4096, 16, 6), (513, 32, 8)])
+def test_fused_sv_matches_two_pass_and_oracle(m, C, D):
+    """The one-pass covariance product (cooperative CTAs, one read of O)
+    against the two-pass kernels and the oracle's centred form, for row
+    counts that leave a partial last block of 16 rows (m = 17, 300, 513),
+    a single row, 3 CTAs (n = 336) and 152 CTAs (n = 74,304)."""
+    v = _ctx(C, D)
+    n = v.n
+    rng = inputs.rng_for(42, m)
+    O = inputs.synthetic_O(m, n, rng)
+    E = inputs.synthetic_E(m, rng)
+    Od = to_dev(O)
+    ob, _, _ = v.sr_moments(Od, to_dev(E))
+    x = np.random.default_rng(5).standard_normal(n)
+    got = v.sr_matvec(Od, ob, to_dev(x), 1e-4).cpu().numpy()
+    v.set_sr_fused(False)
+    two = v.sr_matvec(Od, ob, to_dev(x), 1e-4).cpu().numpy()
+    v.set_sr_fused(True)
+    ref = oracle.sr_matvec_centered(O.astype(np.float64), x, 1e-4)
+    # The fused product centres t = O v with Obar . v, the two-pass one with
+    # the mean of t: equal in exact arithmetic, each within a few double-float
+    # ulps (2^-46) of the uncentred terms (1/m) sum_b |O_bk| |t_b|, the scale
+    # of the rounding (at m = 1, S = 0 and only that rounding remains)
+    Od64 = O.astype(np.float64)
+    mag = np.abs(Od64).T @ np.abs(Od64 @ x) / m
+    assert np.all(np.abs(got - two) <= 1e-13 * mag + 1e-10 * np.abs(two))
+    assert np.all(np.abs(got - ref) <= 1e-13 * mag + 1e-9 * np.abs(ref))
+    # the CG built on either product: 30 steps at shift 1 leave these systems
+    # unconverged (residual ~1e-3 at m = 4096), where rounding alone moves
+    # the iterates apart, so each solve is checked through what CG
+    # guarantees: its reported residual is the true one and is no worse than
+    # the oracle CG's
+    ob64, _, g = oracle.sr_moments(Od64, E)
+    _, rres = oracle.sr_cg(Od64, E, 1.0, 30)
+    for fused in (True, False):
+        v.set_sr_fused(fused)
+        xs, res = v.sr_solve(Od, to_dev(E), 1.0, 30)
+        r = g - oracle.sr_matvec_centered(Od64, xs.cpu().numpy(), 1.0)
+        true_res = np.linalg.norm(r) / max(np.linalg.norm(g), 1e-300)
+        assert true_res <= 1.5 * rres + 1e-10
+        assert abs(res - true_res) <= 0.05 * true_res + 1e-10
+    v.set_sr_fused(True)
