@@ -136,15 +136,27 @@ __global__ void build_kernel(const int8_t *__restrict__ sigma, int64_t b0, int64
             f = s[si] != s[sj];
         }
         const unsigned m = __ballot_sync(0xffffffffu, f);
-        if (f) {
-            const int64_t row = Bc + q + __popc(m & ((1u << lane) - 1u));
-            coef[q + __popc(m & ((1u << lane) - 1u))] = 0.5 * ((k & 3) < 2 ? J1 : J2);
-            int8_t *dst = cfg + 4 * row * N;
-            for (int i = 0; i < 4; ++i)
-                for (int p = 0; p < N; ++p) {
+        if (f) coef[q + __popc(m & ((1u << lane) - 1u))] = 0.5 * ((k & 3) < 2 ? J1 : J2);
+        // the chunk's neighbours one after another, each written by the whole
+        // warp: 4 N bytes as N words of four consecutive bytes, lane-strided
+        // (coalesced); N = L^2 is a multiple of 4 for even L
+        unsigned mm = m;
+        for (int idx = 0; mm; ++idx) {
+            const int src_lane = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            const int bi = __shfl_sync(0xffffffffu, si, src_lane), bj = __shfl_sync(0xffffffffu, sj, src_lane);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(cfg + 4 * (Bc + q + idx) * N);
+            for (int wd = lane; wd < N; wd += 32) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int e = 4 * wd + t, i = e / N, p = e - i * N;
                     const int src = rot_src(L, i, p / L, p % L);
-                    dst[i * N + p] = src == si ? s[sj] : (src == sj ? s[si] : s[src]);
+                    const int8_t v = src == bi ? s[bj] : (src == bj ? s[bi] : s[src]);
+                    word |= (uint32_t)(uint8_t)v << (8 * t);
                 }
+                dst[wd] = word;
+            }
         }
         q += __popc(m);
     }

@@ -456,6 +456,41 @@ static int tc_eloc_cone(vmc_ctx *ctx, const int8_t *sigma, int64_t B, double *ou
     return VMC_OK;
 }
 
+namespace vmc {
+namespace tc {
+
+// Work order of a ragged batch: samples grouped by lattice side, largest
+// first (the longest work starts first and the small lattices fill the tail;
+// slabs hold one lattice side, so grouping also keeps them full), invalid
+// sides last.  One CTA: a histogram, a scan from the largest side down, and
+// a scatter (the order inside a group is immaterial: every sample's results
+// are independent of where it is processed).
+__global__ void ragged_order_kernel(const int32_t *__restrict__ Ls, int64_t B, int L_max, int64_t *order)
+{
+    __shared__ unsigned long long cnt[18];
+    const int nb = 18;   // bins 2..16 (L = 4..32), bin 17 invalid
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    auto bin_of = [&](int L) { return ((L & 1) || L < 4 || L > L_max) ? 17 : (L >> 1); };
+    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) atomicAdd(&cnt[bin_of(Ls[b])], 1ull);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int k = 16; k >= 2; --k) { const unsigned long long c = cnt[k]; cnt[k] = acc; acc += c; }
+        const unsigned long long c = cnt[17];
+        cnt[17] = acc;
+        (void)c;
+    }
+    __syncthreads();
+    for (int64_t b = threadIdx.x; b < B; b += blockDim.x) {
+        const unsigned long long pos = atomicAdd(&cnt[bin_of(Ls[b])], 1ull);
+        order[pos] = b;
+    }
+}
+
+}  // namespace tc
+}  // namespace vmc
+
 int vmc_tc_eloc(vmc_ctx *ctx, int mode, const int8_t *sigma, const int64_t *offs, const int32_t *Ls,
                 int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr, cudaStream_t s)
 {
@@ -465,7 +500,17 @@ int vmc_tc_eloc(vmc_ctx *ctx, int mode, const int8_t *sigma, const int64_t *offs
     const bool ragged = (Ls != nullptr);
     int rc = tc::make_plan(ctx, ragged ? L_max : ctx->L, L_max, ragged, &pl);
     if (rc) return vmc_fail(ctx, rc, "no tensor-core plan for L=%d C=%d", L_max, ctx->arch.channels);
-    return tc::launch_any(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, s);
+    if (!ragged) return tc::launch_any(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr, s);
+    rc = vmc_ensure_ws(ctx, &ctx->order_ws, &ctx->order_ws_bytes, (size_t)B * sizeof(int64_t));
+    if (rc) return rc;
+    int64_t *order = static_cast<int64_t *>(ctx->order_ws);
+    tc::ragged_order_kernel<<<1, 1024, 0, s>>>(Ls, B, L_max, order);
+    ctx->launches += 1;
+    rc = vmc_cuda_check(ctx, cudaGetLastError(), "ragged order");
+    if (rc) return rc;
+    tc::Params p = tc::base_params(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr);
+    p.order = order;
+    return tc::launch_var<tc::VAR_PLAIN>(ctx, pl, p, s);
 }
 
 int vmc_tc_debug_timeout(vmc_ctx *ctx, int64_t budget_ns, cudaStream_t s)

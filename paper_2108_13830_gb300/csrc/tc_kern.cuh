@@ -87,6 +87,7 @@ struct Params {
     const int8_t *sigma;
     const int64_t *offs;
     const int32_t *Ls;
+    const int64_t *order;       // ragged batches: sample of each work item (nullable)
     int L_uniform, L_max;
     int D, marshall;
     double J1, J2;
@@ -995,9 +996,15 @@ struct Kern {
                     act = 0;
                 } else {
                     while (!c.no_more) {
-                        long long b = c.pending_b >= 0 ? c.pending_b : (long long)atomicAdd(p.counter, 1);
+                        long long b = c.pending_b;
                         c.pending_b = -1;
-                        if (b >= p.B) { c.no_more = 1; break; }
+                        if (b < 0) {
+                            // next work item; a ragged batch is walked in the
+                            // order of `order` (largest lattices first)
+                            const long long idx = (long long)atomicAdd(p.counter, 1);
+                            if (idx >= p.B) { c.no_more = 1; break; }
+                            b = p.order ? p.order[idx] : idx;
+                        }
                         const int Lb = p.Ls ? p.Ls[b] : p.L_uniform;
                         if ((Lb & 1) || Lb < 4 || Lb > p.L_max || p.geo[Lb >> 1].G == 0) {
                             p.out_a[b] = nan_d();
