@@ -537,8 +537,18 @@ def side_measurements(torch, VMC, ev, stream, parts=SIDE_PARTS):
             fl = float(sum((1.0 + float(k)) for k in nn.cpu().numpy()[idx])) * f_fwd(int(L), w.C, w.D)
             per_L[str(int(L))] = {"samples": int(len(idx)), "ms": tL, "tflops": fl / (tL / 1e3) / 1e12}
             cl.close()
+        cone_fl = 0.0
+        for L in w.Ls:
+            idx = np.flatnonzero(Ls == L)
+            sigL = np.stack([packed[offs[i]:offs[i] + L * L] for i in idx]).reshape(-1, L, L)
+            b1, b2 = antiparallel_counts(sigL)
+            cone_fl += len(idx) * f_fwd(int(L), w.C, w.D) + cone_flops(int(L), w.C, w.D, float(b1.sum()), float(b2.sum()))
         out["ragged_8_16_fp16"] = {"samples": B, "ms": t_r, "samples_per_s": B / (t_r / 1e3),
-                                   "eloc_tflops": flops / (t_r / 1e3) / 1e12, "launch": "one persistent launch, CUDA graph",
+                                   "light_cone": True,
+                                   "eloc_tflops": cone_fl / (t_r / 1e3) / 1e12,
+                                   "eloc_full_forward_tflops": flops / (t_r / 1e3) / 1e12,
+                                   "launch": ("one graph-replayed call: work-order sort, parent pass, light-cone pass "
+                                              "(all sides in one persistent launch each)"),
                                    "per_L_separate_launches": per_L, "separate_total_ms": t_split}
         ctx.close()
         torch.cuda.empty_cache()

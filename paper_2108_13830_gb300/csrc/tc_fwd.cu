@@ -1,6 +1,7 @@
 // Host side of the tensor-core forward: slab planning, launches, the tile
 // autotuner and diagnostics.  The kernel itself is in tc_kern.cuh.
 #include <algorithm>
+#include <cstring>
 #include <vector>
 #include "tc_kern.cuh"
 
@@ -257,6 +258,73 @@ static int make_cone_plan(const vmc_ctx *ctx, Plan *pl)
     return VMC_OK;
 }
 
+// Light-cone plan for a ragged batch of sides 4 .. L_max: one slab count and
+// lane packing P for the launch (its kernel is compiled for one P), the
+// best number of windows per slab for each side, and the per-side layer
+// geometry as a [L / 2][layer] table.  (S, P) minimise the summed modelled
+// cost of the sides, each weighted by its neighbour count 2 L^2.
+static int make_cone_plan_ragged(const vmc_ctx *ctx, int L_max, Plan *pl, std::vector<LayerGeo> &tab)
+{
+    const int C = ctx->arch.channels, D = ctx->arch.n_layers_cc;
+    if (cone_w(L_max, D) != L_max) return VMC_ERR_UNSUPPORTED;
+    double best = 1e300;
+    int bS = 0, bP = 0;
+    for (int S = 1; S <= 2; ++S) {
+        const uint32_t buf = buf_bytes(C, S, L_max, D);
+        for (int P = 1; P <= MAX_P; ++P) {
+            if (!p_allowed(C, P)) continue;
+            double tot = 0;
+            bool ok = true;
+            for (int L = 4; L <= L_max && ok; L += 2) {
+                double bl = 1e300;
+                for (int G = 1; G <= MAX_SLOTS; ++G) {
+                    int rows_max = 0;
+                    for (int l = 0; l <= D; ++l) {
+                        int rows;
+                        cone_layer(L, l, G, P, &rows);
+                        rows_max = std::max(rows_max, rows);
+                    }
+                    if ((size_t)rows_max * P * C * 2 > buf) break;
+                    bl = std::min(bl, cone_cost(C, L, D, G, P, S));
+                }
+                if (bl >= 1e299) ok = false;
+                else tot += bl * 2.0 * L * L;
+            }
+            if (ok && tot < best - 1e-9) { best = tot; bS = S; bP = P; }
+        }
+    }
+    if (!bS) return VMC_ERR_UNSUPPORTED;
+    pl->S = bS;
+    pl->P = bP;
+    pl->BUF = buf_bytes(C, bS, L_max, D);
+    pl->slotc = bP * C;
+    for (int i = 0; i < 17; ++i) { pl->geo[i] = Geo{0, 0, 0, 0}; pl->cone[i] = LayerGeo{}; }
+    tab.assign(17 * 17, LayerGeo{});
+    for (int L = 4; L <= L_max; L += 2) {
+        double bl = 1e300;
+        int bG = 0;
+        for (int G = 1; G <= MAX_SLOTS; ++G) {
+            int rows_max = 0;
+            for (int l = 0; l <= D; ++l) {
+                int rows;
+                cone_layer(L, l, G, bP, &rows);
+                rows_max = std::max(rows_max, rows);
+            }
+            if ((size_t)rows_max * bP * C * 2 > pl->BUF) break;
+            const double sc = cone_cost(C, L, D, G, bP, bS);
+            if (sc < bl - 1e-9) { bl = sc; bG = G; }
+        }
+        for (int l = 0; l <= D; ++l) {
+            int rows;
+            tab[(L >> 1) * 17 + l] = cone_layer(L, l, bG, bP, &rows);
+        }
+        pl->geo[L >> 1] = Geo{bG, bP, tab[(L >> 1) * 17 + D].T, tab[(L >> 1) * 17 + D].PW};
+    }
+    pl->smem = 2 * (size_t)(18 * C * C) + (size_t)2 * bS * pl->BUF + ctrl_bytes(L_max, C, D);
+    if (pl->smem > SMEM_LIMIT) return VMC_ERR_UNSUPPORTED;
+    return VMC_OK;
+}
+
 // Parameters of one launch that do not depend on the variant.
 static Params base_params(const vmc_ctx *ctx, const Plan &pl, int mode, const int8_t *sigma, const int64_t *offs,
                           const int32_t *Ls, int64_t B, int L_max, double *out_a, void *out_b, int32_t *n_nbr)
@@ -508,6 +576,46 @@ int vmc_tc_eloc(vmc_ctx *ctx, int mode, const int8_t *sigma, const int64_t *offs
     ctx->launches += 1;
     rc = vmc_cuda_check(ctx, cudaGetLastError(), "ragged order");
     if (rc) return rc;
+    // light cone over the ragged batch: every side shares the launch's P;
+    // the parent store is sized for L_max (in one piece, at most 2 GiB)
+    const int C = ctx->arch.channels, D = ctx->arch.n_layers_cc;
+    const long long stride = (long long)D * C * L_max * L_max * 2;
+    tc::Plan pc;
+    std::vector<tc::LayerGeo> tab;
+    if (mode == 1 && ctx->light_cone && (long long)B * stride <= ((long long)2 << 30) &&
+        tc::make_cone_plan_ragged(ctx, L_max, &pc, tab) == VMC_OK) {
+        // the per-side table goes to the device once per plan (before any capture)
+        const size_t tb = tab.size() * sizeof(tc::LayerGeo);
+        const char *th = reinterpret_cast<const char *>(tab.data());
+        if (ctx->cone_tab_host.size() != tb || memcmp(ctx->cone_tab_host.data(), th, tb) != 0) {
+            rc = vmc_ensure_ws(ctx, &ctx->cone_tab, &ctx->cone_tab_bytes, tb);
+            if (rc) return rc;
+            rc = vmc_cuda_check(ctx, cudaMemcpy(ctx->cone_tab, th, tb, cudaMemcpyHostToDevice), "cone table");
+            if (rc) return rc;
+            ctx->cone_tab_host.assign(th, th + tb);
+        }
+        auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+        const size_t need = al((size_t)B * stride) + al((size_t)B * 8) + al((size_t)B);
+        rc = vmc_ensure_ws(ctx, &ctx->cone_ws, &ctx->cone_ws_bytes, need);
+        if (rc) return rc;
+        uint8_t *store = static_cast<uint8_t *>(ctx->cone_ws);
+        double *la = reinterpret_cast<double *>(store + al((size_t)B * stride));
+        int8_t *sg = reinterpret_cast<int8_t *>(reinterpret_cast<uint8_t *>(la) + al((size_t)B * 8));
+        tc::Params p1 = tc::base_params(ctx, pl, 0, sigma, offs, Ls, B, L_max, la, sg, nullptr);
+        p1.order = order;
+        p1.act_store = store;
+        p1.store_stride = stride;
+        rc = tc::launch_store_var(ctx, pl, p1, s);
+        if (rc) return rc;
+        tc::Params p2 = tc::base_params(ctx, pc, 1, sigma, offs, Ls, B, L_max, out_a, nullptr, n_nbr);
+        p2.order = order;
+        p2.act_store = store;
+        p2.store_stride = stride;
+        p2.par_la = la;
+        p2.par_sg = sg;
+        p2.cone_tab = static_cast<const tc::LayerGeo *>(ctx->cone_tab);
+        return tc::launch_cone_var(ctx, pc, p2, s);
+    }
     tc::Params p = tc::base_params(ctx, pl, mode, sigma, offs, Ls, B, L_max, out_a, out_b, n_nbr);
     p.order = order;
     return tc::launch_var<tc::VAR_PLAIN>(ctx, pl, p, s);

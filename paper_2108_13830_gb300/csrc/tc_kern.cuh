@@ -110,6 +110,7 @@ struct Params {
     const double *par_la;       // cone pass: parent log|psi_CNN|
     const int8_t *par_sg;       // cone pass: parent sign of psi_CNN (no Marshall factor)
     LayerGeo cone[17];          // cone pass: per-layer geometry (uniform lattice side)
+    const LayerGeo *cone_tab;   // cone pass over a ragged batch: [L / 2][layer] (device), else null
 };
 
 struct Parent {
@@ -411,11 +412,11 @@ struct Kern {
         m.PS = (p.BUF / (uint32_t)(g.P * CP8 * 16)) * 16u;
     }
 
-    // Geometry of layer l of slab s: per layer for the cone pass (the same
-    // for every slab), one for all layers otherwise.
+    // Geometry of layer l of slab s: per layer for the cone pass (from the
+    // per-side table over a ragged batch), one for all layers otherwise.
     __device__ __forceinline__ const LayerGeo &lg(int s, int l) const
     {
-        if constexpr (VAR == VAR_CONE) return p.cone[l];
+        if constexpr (VAR == VAR_CONE) return p.cone_tab ? p.cone_tab[(c.slab[s].L >> 1) * 17 + l] : p.cone[l];
         else return c.slab[s].g;
     }
 
@@ -542,7 +543,17 @@ struct Kern {
                         if (mw == 0) waited[bsel]++;
                         any = true;
                     }
-                    const int T = (VAR == VAR_CONE) ? p.cone[l].T : *(volatile int *)&c.slab[s].g.T;
+                    int T;
+                    if constexpr (VAR == VAR_CONE) {
+                        if (p.cone_tab) {
+                            const int Ls = *(volatile int *)&c.slab[s].L;
+                            T = p.cone_tab[(Ls >> 1) * 17 + l].T;
+                        } else {
+                            T = p.cone[l].T;
+                        }
+                    } else {
+                        T = *(volatile int *)&c.slab[s].g.T;
+                    }
                     for (int t = 0; t < T; ++t) {
                         const int slot = nslot;
                         const uint32_t use_par = npar;
@@ -607,7 +618,10 @@ struct Kern {
         k.grow = 0;
         k.RWn = 0;
         if constexpr (VAR == VAR_CONE) {
-            if (l < p.D && p.cone[l + 1].w > g0.w) { k.grow = 1; k.RWn = p.cone[l + 1].RW; }
+            if (l < p.D) {
+                const LayerGeo &g1 = lg(s, l + 1);
+                if (g1.w > g0.w) { k.grow = 1; k.RWn = g1.RW; }
+            }
         }
         k.sm = &m;
         k.out = smem_u32(act_buf(s, l & 1));
@@ -902,7 +916,7 @@ struct Kern {
     {
         const SlabMeta &m = c.slab[s];
         const int L = m.L;
-        const LayerGeo &g0 = p.cone[0];
+        const LayerGeo &g0 = lg(s, 0);
         const int w0 = g0.w, PW = g0.PW;
         const uint32_t a0 = smem_u32(act_buf(s, 1));
         const uint32_t PS = m.PS;
@@ -950,7 +964,7 @@ struct Kern {
     {
         const SlabMeta &m = c.slab[s];
         const int L = m.L, N = L * L, count = m.count;
-        const int w = p.cone[l].w, W4 = w + 4, RWn = p.cone[l + 1].RW;
+        const int w = lg(s, l).w, W4 = w + 4, RWn = lg(s, l + 1).RW;
         const int per = 8 * w + 16;   // ring cells per window
         const uint32_t out = smem_u32(act_buf(s, l & 1));
         const uint32_t PS = m.PS;

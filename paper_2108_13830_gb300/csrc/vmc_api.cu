@@ -126,7 +126,7 @@ void vmc_destroy(vmc_ctx *ctx)
     cudaFree(ctx->theta64); cudaFree(ctx->theta32); cudaFree(ctx->wsimt); cudaFree(ctx->wsimtT);
     cudaFree(ctx->bias); cudaFree(ctx->bias32); cudaFree(ctx->wimg);
     cudaFree(ctx->status); cudaFree(ctx->counter);
-    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws); cudaFree(ctx->sym_ws); cudaFree(ctx->sym_cnt); cudaFree(ctx->cone_ws); cudaFree(ctx->order_ws);
+    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws); cudaFree(ctx->sym_ws); cudaFree(ctx->sym_cnt); cudaFree(ctx->cone_ws); cudaFree(ctx->order_ws); cudaFree(ctx->cone_tab);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
     delete ctx;
 }

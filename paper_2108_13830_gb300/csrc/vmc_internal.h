@@ -74,6 +74,9 @@ struct vmc_ctx {
     size_t sym_cnt_bytes = 0;
     void *order_ws = nullptr;    // ragged batches: work order (largest lattices first)
     size_t order_ws_bytes = 0;
+    void *cone_tab = nullptr;    // ragged light cone: per-side layer geometry (device)
+    size_t cone_tab_bytes = 0;
+    std::vector<char> cone_tab_host;   // the table last uploaded
     void *cone_ws = nullptr;     // light-cone E_loc: parent activations, log|psi| and signs
     size_t cone_ws_bytes = 0;
     int light_cone = 1;          // evaluate E_loc neighbours incrementally where it applies

@@ -181,3 +181,33 @@ def test_cone_tile_choices_and_autotune(L, C, D, prec):
     e2, _ = v.local_energy(s)
     assert v.sync_status()[0] == VMC_OK
     np.testing.assert_array_equal(e2.cpu().numpy(), e0)
+
+
+def test_cone_ragged_batch_bitwise():
+    """A mixed batch of sides 4 .. 16 (one persistent launch walking the
+    samples largest side first): the light cone gives the plain ragged
+    evaluation's results bit for bit, and sides beyond L_max stay NaN with
+    VMC_ERR_ARG."""
+    w = inputs.Workload("cone_rag", 16, 16, 6, "fp16", 96, kind="ragged", Ls=(4, 6, 8, 12, 16), index=83)
+    packed, offs, Ls, theta = inputs.ragged_inputs(w)
+    v = make_ctx(w, theta=theta, L=16)
+    pk, of, Lt = to_dev(packed), to_dev(offs), to_dev(Ls)
+    v.set_light_cone(True)
+    e1, n1 = v.local_energy_ragged(pk, of, Lt, 16)
+    r1 = v.sync_status()
+    v.set_light_cone(False)
+    e0, n0 = v.local_energy_ragged(pk, of, Lt, 16)
+    r0 = v.sync_status()
+    v.set_light_cone(True)
+    assert r1 == r0 == (VMC_OK, 0)
+    np.testing.assert_array_equal(n1.cpu().numpy(), n0.cpu().numpy())
+    np.testing.assert_array_equal(e1.cpu().numpy(), e0.cpu().numpy())
+    # the same launch with L_max = 12: the side-16 samples are refused
+    e2, _ = v.local_energy_ragged(pk, of, Lt, 12)
+    r2 = v.sync_status()
+    from paper_2108_13830_gb300.binding import VMC_ERR_ARG
+    assert r2[0] == VMC_ERR_ARG
+    e2 = e2.cpu().numpy()
+    big = Ls == 16
+    assert np.all(np.isnan(e2[big]))
+    np.testing.assert_array_equal(e2[~big], e0.cpu().numpy()[~big])
