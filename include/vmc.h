@@ -260,6 +260,27 @@ int vmc_set_sr_fused(vmc_ctx *ctx, int enable);
 int vmc_sr_solve(vmc_ctx *ctx, const float *O_dev, const double *eloc_dev, int64_t m,
                  double shift, int iters, double *x_dev, double *resid_out, void *stream);
 
+/* The same SR direction x = (S + shift I)^{-1} G solved exactly (no
+ * iteration) in the m-dimensional sample space, the choice for m << n
+ * (Sec. 2.1, Eq. 6-7; Sec. 3.2.2 factors the covariance by Cholesky): by
+ * the Woodbury identity, with Oc = O - 1 Obar^T,
+ *     x = (G - Oc^T y) / shift,   (m shift I + Oc Oc^T) y = Oc G.
+ * The m x m Gram matrix Oc Oc^T is formed on the device from the centred
+ * rows held as double-float pairs (FP64-level accuracy), factored by a
+ * blocked FP64 Cholesky and solved; Oc G and Oc^T y are passes over O.
+ * Dividing G - Oc^T y by the shift amplifies rounding by the condition of
+ * S + shift I, so two steps of iterative refinement follow (r = G -
+ * (S + shift I) x with the covariance product of vmc_sr_matvec, x += W r,
+ * W the same solve applied to r).
+ * Workspace: 8 m n + 8 m^2 bytes (3.2 GB at m = 4096, n = 92,800).  Cost
+ * grows as m^2 n: use it where m is well below n.  shift > 0; m <= 65536.
+ * x_dev double [n]; resid_out (host, nullable): ||G - (S + shift I) x|| /
+ * ||G|| from one more covariance product (synchronises `stream`).  A
+ * factorisation that meets a non-positive pivot leaves NaN in x and raises
+ * VMC_ERR_NONFINITE in vmc_sync_status. */
+int vmc_sr_solve_dense(vmc_ctx *ctx, const float *O_dev, const double *eloc_dev, int64_t m, double shift,
+                       double *x_dev, double *resid_out, void *stream);
+
 /* The SR parameter update of Eq. 6, theta <- theta - eta x, on the
  * context's FP64 parameter vector, with x the direction vmc_sr_solve
  * returns (Delta = eta x, x = (S + shift I)^{-1} G).  Each entry is

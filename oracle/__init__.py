@@ -165,6 +165,19 @@ def sr_cg(O, E, shift, iters):
     return x, float(res)
 
 
+def sr_solve_dense(O, E, shift):
+    """x = (M + shift I)^{-1} G with M the covariance of Eq. 7 formed as an
+    n x n matrix and factored by Cholesky (LAPACK potrf/potrs through
+    scipy), the dense route of Sec. 3.2.2.  Small n only (n^2 doubles)."""
+    import scipy.linalg as sla
+    O = _f64(O)
+    m, n = O.shape
+    ob, _, g = sr_moments(O, E)
+    Oc = O - ob
+    M = (Oc.T @ Oc) / m + float(shift) * _np.eye(n)
+    return sla.cho_solve(sla.cho_factor(M, lower=True), g)
+
+
 def sr_update(theta, x, eta):
     """theta - eta x: the parameter step of Eq. 6 (Delta = eta x)."""
     return _f64(theta) - float(eta) * _f64(x)

@@ -65,6 +65,7 @@ _SIGS = {
     "vmc_set_wait_budget": (_I, [_P, _I64]),
     "vmc_set_light_cone": (_I, [_P, _I]),
     "vmc_set_sr_fused": (_I, [_P, _I]),
+    "vmc_sr_solve_dense": (_I, [_P, _P, _P, _I64, _D, _P, _P, _P]),
     "vmc_set_cone_tiles": (_I, [_P, _P]),
     "vmc_get_cone_tiles": (_I, [_P, _P]),
     "vmc_set_launch_timing": (_I, [_P, _I]),
@@ -267,6 +268,16 @@ class VMC:
         out = torch.empty(self.n, dtype=torch.float64, device=O.device)
         self._check(lib().vmc_ot_vec(self._h, _ptr(O), O.shape[0], _ptr(w), _ptr(out), _stream()))
         return out
+
+    def sr_solve_dense(self, O, E, shift=1e-4, out=None, resid=True):
+        """x = (S + shift I)^{-1} G solved exactly in sample space (Woodbury)."""
+        O = _dev(O, torch.float32, "O")
+        E = _dev(E, torch.float64, "E")
+        x = out if out is not None else torch.empty(self.n, dtype=torch.float64, device=O.device)
+        r = ct.c_double(0.0)
+        self._check(lib().vmc_sr_solve_dense(self._h, _ptr(O), _ptr(E), O.shape[0], float(shift), _ptr(x),
+                                             ct.byref(r) if resid else None, _stream()))
+        return x, (r.value if resid else None)
 
     def sr_solve(self, O, E, shift=1e-4, iters=50, out=None, resid=True):
         O = _dev(O, torch.float32, "O")

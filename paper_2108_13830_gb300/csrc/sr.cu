@@ -11,6 +11,8 @@
 // (1/m) O^T (t - tbar 1) with t = O v and tbar = (1/m) sum_b t_b, which is
 // the same quantity (Obar . v = tbar).
 #include <algorithm>
+#include <cmath>
+#include <vector>
 #include "vmc_internal.h"
 #include "tc_ptx.cuh"
 
@@ -855,5 +857,338 @@ int vmc_sr_solve_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m, 
         rc = vmc_cuda_check(ctx, cudaStreamSynchronize(s), "sync");
         if (rc) return rc;
     }
+    return VMC_OK;
+}
+
+// ---------------------------------------------------------------- sample-space solve
+//
+// (S + shift I) x = G solved exactly in the m-dimensional sample space
+// (Woodbury): with Oc = O - 1 Obar^T (the centred rows) and S = Oc^T Oc / m,
+//     x = (G - Oc^T y) / shift,   (m shift I + Oc Oc^T) y = Oc G.
+// The m x m Gram matrix K = Oc Oc^T is formed from the centred rows held as
+// double-float pairs (one exact subtraction per element), K + m shift I is
+// factored by a blocked FP64 Cholesky, and the two triangular solves and
+// the two passes over O (Oc G, Oc^T y) complete the solve.  Sec. 3.2.2 does
+// the same solve with a dense n x n Cholesky; for m << n the m x m system
+// is the cheaper exact route.
+
+namespace vmc {
+namespace dense {
+
+constexpr int TB = 64;        // Gram tile (TB x TB outputs per CTA, 256 threads of 4 x 4)
+constexpr int TK = 16;        // columns per shared-memory stage
+constexpr int NB = 32;        // Cholesky block
+
+// Oc[b][k] = O[b][k] - Obar[k] as a double-float pair: the difference of the
+// float O and the high part of Obar is exact (TwoSum), then the low part of
+// Obar is taken off
+__global__ void center_rows_kernel(const float *__restrict__ O, int64_t m, int64_t n, const double *__restrict__ Obar,
+                                   float2 *__restrict__ Oc)
+{
+    const int64_t tot = m * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e % n;
+        float oh, ol;
+        split(Obar[k], oh, ol);
+        float s, err;
+        two_sum(O[e], -oh, s, err);
+        err -= ol;
+        float h, l;
+        fast_two_sum(s, err, h, l);
+        Oc[e] = make_float2(h, l);
+    }
+}
+
+// K[a][b] = sum_k Oc[a][k] Oc[b][k] (+ diag on a = b) for the lower
+// triangle, tile by tile: (ah + al)(bh + bl) with ah bh exact by FMA, the
+// cross terms and the running sum's rounding collected in the low word.
+__global__ void __launch_bounds__(256) gram_df_kernel(const float2 *__restrict__ Oc, int64_t m, int64_t n, double diag,
+                                                      double *__restrict__ K)
+{
+    // tile (I, J), I >= J, from the linear block index
+    const int64_t t = blockIdx.x;
+    int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int64_t J = t - I * (I + 1) / 2;
+    __shared__ float2 As[2][TK][TB], Bs[2][TK][TB];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t a0 = I * TB, b0 = J * TB;
+    float ah[4][4], al[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { ah[i][j] = 0.f; al[i][j] = 0.f; }
+    // each thread stages 4 elements of each tile per chunk: row tid / 4, columns 4 (tid % 4) ..
+    auto load = [&](int buf, int64_t k0) {
+        const int r = tid >> 2, c0 = (tid & 3) * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t k = k0 + c0 + q;
+            const int64_t ra = a0 + r, rb = b0 + r;
+            As[buf][c0 + q][r] = (ra < m && k < n) ? Oc[ra * n + k] : make_float2(0.f, 0.f);
+            Bs[buf][c0 + q][r] = (rb < m && k < n) ? Oc[rb * n + k] : make_float2(0.f, 0.f);
+        }
+    };
+    load(0, 0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += TK) {
+        if (k0 + TK < n) load(buf ^ 1, k0 + TK);
+#pragma unroll 4
+        for (int kk = 0; kk < TK; ++kk) {
+            float2 av[4], bv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = As[buf][kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[buf][kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float p = av[i].x * bv[j].x;
+                    float pe = fmaf(av[i].x, bv[j].x, -p);
+                    pe = fmaf(av[i].x, bv[j].y, pe);
+                    pe = fmaf(av[i].y, bv[j].x, pe);
+                    float s, e;
+                    two_sum(ah[i][j], p, s, e);
+                    ah[i][j] = s;
+                    al[i][j] += e + pe;
+                }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
+            if (a < m && b < m && b <= a) K[a * m + b] = (double)ah[i][j] + (double)al[i][j] + (a == b ? diag : 0.0);
+        }
+}
+
+// Cholesky of the NB x NB diagonal block k (lower, in place); a pivot that
+// is not positive makes the factor NaN and raises VMC_STATUS_NONFINITE
+__global__ void potrf_diag_kernel(double *K, int64_t m, int k, DevStatus *st)
+{
+    __shared__ double Ls[NB][NB + 1];
+    const int i = threadIdx.x;   // row of the block
+    const int64_t base = (int64_t)k * NB;
+    const int nb = (int)min((int64_t)NB, m - base);
+    if (i < nb)
+        for (int j = 0; j <= i; ++j) Ls[i][j] = K[(base + i) * m + base + j];
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (i == j) {
+            double d = Ls[j][j];
+            for (int t = 0; t < j; ++t) d -= Ls[j][t] * Ls[j][t];
+            if (!(d > 0.0)) {
+                atomicOr(&st->flags, VMC_STATUS_NONFINITE);
+                d = __longlong_as_double(0x7ff8000000000000LL);
+            }
+            Ls[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        if (i > j && i < nb) {
+            double v = Ls[i][j];
+            for (int t = 0; t < j; ++t) v -= Ls[i][t] * Ls[j][t];
+            Ls[i][j] = v / Ls[j][j];
+        }
+        __syncthreads();
+    }
+    if (i < nb)
+        for (int j = 0; j <= i; ++j) K[(base + i) * m + base + j] = Ls[i][j];
+}
+
+// panel below block k: row r solves x L_kk^T = K[r][block k] by forward substitution
+__global__ void trsm_panel_kernel(double *K, int64_t m, int k)
+{
+    __shared__ double Ls[NB][NB + 1];
+    const int64_t base = (int64_t)k * NB;
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        const int i = e / NB, j = e % NB;
+        Ls[i][j] = (j <= i) ? K[(base + i) * m + base + j] : 0.0;
+    }
+    __syncthreads();
+    const int64_t r = base + NB + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    double x[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) x[j] = K[r * m + base + j];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        double v = x[j];
+        for (int t = 0; t < j; ++t) v -= x[t] * Ls[j][t];
+        x[j] = v / Ls[j][j];
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) K[r * m + base + j] = x[j];
+}
+
+// trailing update of the lower triangle: K[i][j] -= sum_t P[i][t] P[j][t]
+// over the panel columns of block k, for i >= j >= (k + 1) NB; 32 x 32 tiles
+__global__ void __launch_bounds__(256) syrk_update_kernel(double *K, int64_t m, int k)
+{
+    const int64_t off = (int64_t)(k + 1) * NB;
+    const int64_t t = blockIdx.x;
+    int64_t I = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((I + 1) * (I + 2) / 2 <= t) ++I;
+    while (I * (I + 1) / 2 > t) --I;
+    const int64_t J = t - I * (I + 1) / 2;
+    __shared__ double Pi[NB][NB + 1], Pj[NB][NB + 1];
+    const int64_t i0 = off + I * 32, j0 = off + J * 32, pc = (int64_t)k * NB;
+    for (int e = threadIdx.x; e < 32 * NB; e += blockDim.x) {
+        const int r = e / NB, c = e % NB;
+        Pi[r][c] = (i0 + r < m) ? K[(i0 + r) * m + pc + c] : 0.0;
+        Pj[r][c] = (j0 + r < m) ? K[(j0 + r) * m + pc + c] : 0.0;
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 8 row groups of 4
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = ty * 4 + q;
+        const int64_t i = i0 + r, j = j0 + tx;
+        if (i >= m || j >= m || j > i) continue;
+        double acc = 0.0;
+#pragma unroll 8
+        for (int c = 0; c < NB; ++c) acc += Pi[r][c] * Pj[tx][c];
+        K[i * m + j] -= acc;
+    }
+}
+
+// L w = z then L^T y = w, one CTA, column by column (L lower, row-major)
+__global__ void __launch_bounds__(1024) chol_solve_kernel(const double *__restrict__ L, int64_t m, double *z)
+{
+    __shared__ double piv;
+    for (int64_t i = 0; i < m; ++i) {
+        if (threadIdx.x == 0) { z[i] /= L[i * m + i]; piv = z[i]; }
+        __syncthreads();
+        const double w = piv;
+        for (int64_t j = i + 1 + threadIdx.x; j < m; j += blockDim.x) z[j] -= L[j * m + i] * w;
+        __syncthreads();
+    }
+    for (int64_t i = m - 1; i >= 0; --i) {
+        if (threadIdx.x == 0) { z[i] /= L[i * m + i]; piv = z[i]; }
+        __syncthreads();
+        const double y = piv;
+        for (int64_t j = threadIdx.x; j < i; j += blockDim.x) z[j] -= L[i * m + j] * y;
+        __syncthreads();
+    }
+}
+
+// z[b] = hi[b] + lo[b] (a double from its split)
+__global__ void join_kernel(const float *__restrict__ hi, const float *__restrict__ lo, int64_t m, double *z)
+{
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < m; b += (int64_t)gridDim.x * blockDim.x)
+        z[b] = (double)hi[b] + (double)lo[b];
+}
+
+// x = (b - sum_chunks u) / shift, or x += that when accumulate
+__global__ void finish_x_kernel(const double *__restrict__ part, int nchunk, int64_t n, const double *__restrict__ b,
+                                double inv_shift, double *x, int accumulate)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        double u = 0.0;
+        for (int c = 0; c < nchunk; ++c) u += part[(int64_t)c * n + k];
+        const double d = (b[k] - u) * inv_shift;
+        x[k] = accumulate ? x[k] + d : d;
+    }
+}
+
+// r = G - q
+__global__ void sub_kernel(const double *__restrict__ G, const double *__restrict__ q, int64_t n, double *r)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        r[k] = G[k] - q[k];
+}
+
+}  // namespace dense
+}  // namespace vmc
+
+int vmc_sr_solve_dense_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m, double shift, double *x,
+                            double *resid_out, cudaStream_t s)
+{
+    using namespace vmc::dense;
+    SrWs w;
+    int rc = sr_workspace(ctx, m, &w);
+    if (rc) return rc;
+    const int64_t n = ctx->n, nch = nchunks_for(m);
+    const int64_t rpc = (m + nch - 1) / nch;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t need = al((size_t)m * n * sizeof(float2)) + al((size_t)m * m * sizeof(double)) + al((size_t)m * 8);
+    rc = vmc_ensure_ws(ctx, &ctx->dense_ws, &ctx->dense_ws_bytes, need);
+    if (rc) return rc;
+    char *base = static_cast<char *>(ctx->dense_ws);
+    float2 *Oc = reinterpret_cast<float2 *>(base);
+    double *K = reinterpret_cast<double *>(base + al((size_t)m * n * sizeof(float2)));
+    double *z = reinterpret_cast<double *>(reinterpret_cast<char *>(K) + al((size_t)m * m * sizeof(double)));
+    // moments: Obar, Ebar, G
+    launch_moments(ctx, O, E, m, w, w.Obar, w.scal + 0, w.G, s);
+    const int g = (int)std::min<int64_t>((n + 255) / 256, 4 * ctx->sm_count);
+    (void)rpc;
+    // K = Oc Oc^T + m shift I (lower triangle), then its Cholesky factor in place
+    center_rows_kernel<<<8 * ctx->sm_count, 256, 0, s>>>(O, m, n, w.Obar, Oc);
+    const int64_t nt = (m + TB - 1) / TB;
+    gram_df_kernel<<<(unsigned)(nt * (nt + 1) / 2), 256, 0, s>>>(Oc, m, n, (double)m * shift, K);
+    ctx->launches += 2;
+    const int nblk = (int)((m + NB - 1) / NB);
+    for (int k = 0; k < nblk; ++k) {
+        potrf_diag_kernel<<<1, NB, 0, s>>>(K, m, k, ctx->status);
+        ctx->launches += 1;
+        const int64_t below = m - (int64_t)(k + 1) * NB;
+        if (below > 0) {
+            trsm_panel_kernel<<<(unsigned)((below + 127) / 128), 128, 0, s>>>(K, m, k);
+            const int64_t tt = (below + 31) / 32;
+            syrk_update_kernel<<<(unsigned)(tt * (tt + 1) / 2), 256, 0, s>>>(K, m, k);
+            ctx->launches += 2;
+        }
+    }
+    // W b = (b - Oc^T y) / shift with (m shift I + K) y = Oc b, the exact
+    // inverse of S + shift I applied to b (accumulated into x when acc)
+    const bool vec = vec_ok(O, n);
+    const int V = vec ? 4 : 1;
+    auto apply = [&](const double *b, int acc) {
+        // z = Oc b (the rows' dots with b, centred on their mean)
+        split_kernel<<<g, 256, 0, s>>>(b, n, w.vh, w.vl);
+        const unsigned rows_grid = (unsigned)((m + 7) / 8);
+        if (vec) rowdot_blk_kernel<8><<<rows_grid, 256, 0, s>>>(O, m, n, w.vh, w.vl, w.t);
+        else rowdot_kernel<false><<<rows_grid, 256, 0, s>>>(O, m, n, w.vh, w.vl, w.t);
+        center_kernel<<<1, 1024, 0, s>>>(w.t, m, 1.0, w.scal + 1, w.wh, w.wl);
+        join_kernel<<<(unsigned)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, s>>>(w.wh, w.wl, m, z);
+        chol_solve_kernel<<<1, 1024, 0, s>>>(K, m, z);
+        // Oc^T y = O^T (y - mean y)
+        center_kernel<<<1, 1024, 0, s>>>(z, m, 1.0, w.scal + 1, w.wh, w.wl);
+        dim3 grid((unsigned)((n / V + 127) / 128), (unsigned)nch);
+        if (vec) colsum_kernel<true, true><<<grid, 128, 0, s>>>(O, m, n, rpc, w.wh, w.wl, nullptr, w.part2);
+        else colsum_kernel<false, true><<<grid, 128, 0, s>>>(O, m, n, rpc, w.wh, w.wl, nullptr, w.part2);
+        finish_x_kernel<<<g, 256, 0, s>>>(w.part2, (int)nch, n, b, 1.0 / shift, x, acc);
+        ctx->launches += 8;
+    };
+    apply(w.G, 0);
+    // The formula divides G - Oc^T y by the shift, so its rounding is
+    // amplified by the condition of S + shift I (residuals ~1e-5 at shift
+    // 1e-4 on these matrices).  Iterative refinement with the double-float
+    // covariance product removes that: r = G - (S + shift I) x, x += W r.
+    for (int it = 0; it < ctx->dense_refine; ++it) {
+        rc = vmc_sr_matvec_impl(ctx, O, m, w.Obar, x, shift, w.q, s);
+        if (rc) return rc;
+        sub_kernel<<<g, 256, 0, s>>>(w.G, w.q, n, w.r);
+        ctx->launches += 1;
+        apply(w.r, 1);
+    }
+    rc = vmc_cuda_check(ctx, cudaGetLastError(), "dense SR solve");
+    if (rc || !resid_out) return rc;
+    // ||G - (S + shift I) x|| / ||G|| with one more covariance product
+    rc = vmc_sr_matvec_impl(ctx, O, m, w.Obar, x, shift, w.q, s);
+    if (rc) return rc;
+    std::vector<double> hq(n), hg(n);
+    rc = vmc_cuda_check(ctx, cudaMemcpyAsync(hq.data(), w.q, n * 8, cudaMemcpyDeviceToHost, s), "resid copy");
+    if (!rc) rc = vmc_cuda_check(ctx, cudaMemcpyAsync(hg.data(), w.G, n * 8, cudaMemcpyDeviceToHost, s), "resid copy");
+    if (!rc) rc = vmc_cuda_check(ctx, cudaStreamSynchronize(s), "sync");
+    if (rc) return rc;
+    double rr = 0, gg = 0;
+    for (int64_t k = 0; k < n; ++k) { rr += (hg[k] - hq[k]) * (hg[k] - hq[k]); gg += hg[k] * hg[k]; }
+    *resid_out = gg > 0 ? sqrt(rr / gg) : 0.0;
     return VMC_OK;
 }

@@ -126,7 +126,7 @@ void vmc_destroy(vmc_ctx *ctx)
     cudaFree(ctx->theta64); cudaFree(ctx->theta32); cudaFree(ctx->wsimt); cudaFree(ctx->wsimtT);
     cudaFree(ctx->bias); cudaFree(ctx->bias32); cudaFree(ctx->wimg);
     cudaFree(ctx->status); cudaFree(ctx->counter);
-    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws); cudaFree(ctx->sym_ws); cudaFree(ctx->sym_cnt); cudaFree(ctx->cone_ws); cudaFree(ctx->order_ws); cudaFree(ctx->cone_tab);
+    cudaFree(ctx->ws); cudaFree(ctx->sr_ws); cudaFree(ctx->mc_ws); cudaFree(ctx->sym_ws); cudaFree(ctx->sym_cnt); cudaFree(ctx->cone_ws); cudaFree(ctx->order_ws); cudaFree(ctx->cone_tab); cudaFree(ctx->dense_ws);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
     delete ctx;
 }
@@ -300,6 +300,18 @@ int vmc_sr_solve(vmc_ctx *ctx, const float *O_dev, const double *eloc_dev, int64
     if (!(shift >= 0.0)) return vmc_fail(ctx, VMC_ERR_ARG, "shift must be >= 0");
     if (!O_dev || !eloc_dev || !x_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
     return vmc_sr_solve_impl(ctx, O_dev, eloc_dev, m, shift, iters, x_dev, resid_out, (cudaStream_t)stream);
+}
+
+int vmc_sr_solve_dense(vmc_ctx *ctx, const float *O_dev, const double *eloc_dev, int64_t m, double shift,
+                       double *x_dev, double *resid_out, void *stream)
+{
+    if (!ctx) return VMC_ERR_ARG;
+    ctx->launches = 0;
+    if (m < 1) return vmc_fail(ctx, VMC_ERR_ARG, "m must be >= 1");
+    if (!(shift > 0.0)) return vmc_fail(ctx, VMC_ERR_ARG, "shift must be > 0");
+    if (!O_dev || !eloc_dev || !x_dev) return vmc_fail(ctx, VMC_ERR_ARG, "null pointer");
+    if (m > 65536) return vmc_fail(ctx, VMC_ERR_UNSUPPORTED, "m = %lld beyond the dense solve's limit", (long long)m);
+    return vmc_sr_solve_dense_impl(ctx, O_dev, eloc_dev, m, shift, x_dev, resid_out, (cudaStream_t)stream);
 }
 
 int vmc_sr_update(vmc_ctx *ctx, const double *x_dev, double eta, void *stream)

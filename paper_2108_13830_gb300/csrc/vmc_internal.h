@@ -72,6 +72,9 @@ struct vmc_ctx {
     size_t sym_ws_bytes = 0;
     void *sym_cnt = nullptr;     // per-sample neighbour counts, diagonals, offsets
     size_t sym_cnt_bytes = 0;
+    int dense_refine = 2;        // sample-space SR solve: refinement steps
+    void *dense_ws = nullptr;    // sample-space SR solve: centred rows, Gram matrix / factor
+    size_t dense_ws_bytes = 0;
     void *order_ws = nullptr;    // ragged batches: work order (largest lattices first)
     size_t order_ws_bytes = 0;
     void *cone_tab = nullptr;    // ragged light cone: per-side layer geometry (device)
@@ -155,6 +158,8 @@ int vmc_sr_matvec_impl(vmc_ctx *ctx, const float *O, int64_t m, const double *Ob
 int vmc_ot_vec_impl(vmc_ctx *ctx, const float *O, int64_t m, const double *w, double *out, cudaStream_t s);
 int vmc_sr_solve_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m, double shift,
                       int iters, double *x, double *resid_out, cudaStream_t s);
+int vmc_sr_solve_dense_impl(vmc_ctx *ctx, const float *O, const double *E, int64_t m, double shift, double *x,
+                            double *resid_out, cudaStream_t s);
 
 __host__ __device__ static inline bool vmc_is_tc(int precision) { return precision == VMC_BF16 || precision == VMC_FP16; }
 __host__ __device__ static inline int64_t vmc_nparams(int C, int D) { return (int64_t)10 * C + (int64_t)D * (9 * C * C + C); }

@@ -6,7 +6,7 @@ import torch
 
 import oracle
 from paper_2108_13830_gb300 import inputs
-from paper_2108_13830_gb300.binding import VMC
+from paper_2108_13830_gb300.binding import VMC, VMC_OK
 from gpu_util import to_dev
 
 pytestmark = pytest.mark.gpu
@@ -156,3 +156,43 @@ def test_fused_sv_matches_two_pass_and_oracle(m, C, D):
         assert true_res <= 1.5 * rres + 1e-10
         assert abs(res - true_res) <= 0.05 * true_res + 1e-10
     v.set_sr_fused(True)
+
+
+@pytest.mark.parametrize("m,C,D,shift", [(64, 4, 2, 1e-2), (300, 4, 2, 1e-4), (1000, 4, 2, 1e-3)])
+def test_dense_solve_vs_oracle_cholesky(m, C, D, shift):
+    """The sample-space (Woodbury) solve against the oracle's dense n x n
+    Cholesky of the covariance (Sec. 3.2.2), for m < n and m > n (n = 336)."""
+    v = _ctx(C, D)
+    rng = inputs.rng_for(44, m)
+    O = inputs.synthetic_O(m, v.n, rng)
+    E = inputs.synthetic_E(m, rng)
+    x, res = v.sr_solve_dense(to_dev(O), to_dev(E), shift)
+    assert v.sync_status()[0] == VMC_OK
+    rx = oracle.sr_solve_dense(O.astype(np.float64), E, shift)
+    x = x.cpu().numpy()
+    assert np.linalg.norm(x - rx) <= 1e-8 * np.linalg.norm(rx)
+    assert res <= 1e-7   # rounding times the condition of S + shift I (~1e8 at shift 1e-4)
+
+
+@pytest.mark.parametrize("m,shift", [(200, 1e-4), (4096, 1e-4)])
+def test_dense_solve_exact_where_cg_is_not(m, shift):
+    """n = 14,080: the dense n x n route is too large for the test, so the
+    solve is checked through its true residual with the oracle's centred
+    covariance product: exact to rounding (after refinement), where fifty
+    CG steps at shift 1e-4 stop near 1e-3 for m = 4096."""
+    v = _ctx(16, 6)
+    rng = inputs.rng_for(45, m)
+    O = inputs.synthetic_O(m, v.n, rng)
+    E = inputs.synthetic_E(m, rng)
+    Od = O.astype(np.float64)
+    x, res = v.sr_solve_dense(to_dev(O), to_dev(E), shift)
+    assert v.sync_status()[0] == VMC_OK
+    _, _, g = oracle.sr_moments(Od, E)
+    r = g - oracle.sr_matvec_centered(Od, x.cpu().numpy(), shift)
+    true_res = np.linalg.norm(r) / np.linalg.norm(g)
+    assert true_res <= 1e-7, true_res
+    assert abs(res - true_res) <= 0.5 * true_res + 1e-10
+    _, cg_res = v.sr_solve(to_dev(O), to_dev(E), shift, 50)
+    # with m = 200 samples CG meets a 200-dimensional Krylov space and
+    # converges in 50 steps; with m = 4096 it is still near 1e-3
+    assert true_res < 1e-2 * cg_res or cg_res < 1e-10

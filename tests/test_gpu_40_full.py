@@ -237,6 +237,15 @@ def test_l24_log_derivs_and_sr(l24):
     # FP32-level arithmetic would miss by 1e-7
     np.testing.assert_allclose(sv, rsv, rtol=1e-9, atol=1e-10 * np.abs(rsv).max())
 
+    # the sample-space (Woodbury) solve, exact: its true residual
+    xd, resd = v.sr_solve_dense(O, e, w.shift)
+    assert v.sync_status()[0] == VMC_OK
+    rd = rg - oracle.sr_matvec_centered(Od, xd.cpu().numpy(), w.shift)
+    true_d = np.linalg.norm(rd) / np.linalg.norm(rg)
+    assert true_d <= 1e-6, true_d
+    # both residuals are near the 1e-11 accuracy of the covariance products
+    assert abs(resd - true_d) <= 0.5 * true_d + 1e-10
+
     # the CG solve, through the true residual of its x
     x, res = v.sr_solve(O, e, w.shift, w.cg_iters)
     assert v.sync_status()[0] == VMC_OK

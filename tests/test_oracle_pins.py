@@ -411,6 +411,27 @@ def test_cg_matches_dense_cholesky():
     assert res < 1e-9
 
 
+def test_dense_solve_pins():
+    """The dense Cholesky solve (Sec. 3.2.2): its x satisfies
+    (M + shift I) x = G through the oracle's own covariance product, equals
+    the converged CG, and equals the sample-space (Woodbury) form
+    x = (G - Oc^T (m shift I + Oc Oc^T)^{-1} Oc G) / shift written out with
+    numpy, for m < n and m > n."""
+    for m, n in ((64, 40), (30, 80)):
+        O, E = _sr_case(m=m, n=n, seed=41 + m)
+        shift = 1e-2
+        x = oracle.sr_solve_dense(O, E, shift)
+        ob, _, g = oracle.sr_moments(O, E)
+        np.testing.assert_allclose(oracle.sr_matvec(O, ob, x, shift), g, rtol=1e-9, atol=1e-11 * np.abs(g).max())
+        xc, res = oracle.sr_cg(O, E, shift, 400)
+        np.testing.assert_allclose(x, xc, rtol=1e-7, atol=1e-9 * np.abs(x).max())
+        Oc = O - O.mean(axis=0)
+        K = Oc @ Oc.T
+        y = np.linalg.solve(m * shift * np.eye(m) + K, Oc @ g)
+        xw = (g - Oc.T @ y) / shift
+        np.testing.assert_allclose(x, xw, rtol=1e-8, atol=1e-10 * np.abs(x).max())
+
+
 def test_cg_single_sample_is_zero():
     """m = 1: M = 0 and G = 0, so the solve returns x = 0."""
     O, E = _sr_case(m=1, n=10)
