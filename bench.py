@@ -229,6 +229,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--eloc-only", action="store_true",
                     help="profiling case: only the local-energy launch, no JSON contract line")
+    ap.add_argument("--odiff-only", action="store_true",
+                    help="profiling case: only the O_k (log-derivative) launch, no JSON contract line")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
     ap.add_argument("--precision", default="", help="override the tensor-core operand type (bf16 | fp16)")
     ap.add_argument("--side", default="", choices=("",) + SIDE_PARTS,
@@ -261,6 +263,8 @@ def main():
     prec = args.precision or ("bf16" if w.precision in ("bf16", "fp32") else w.precision)
     if args.eloc_only:
         return eloc_only(args, w, sig, theta, prec)
+    if args.odiff_only:
+        return odiff_only(args, w, sig, theta, prec)
     if args.side:
         ev0 = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
         print(json.dumps(side_measurements(torch, VMC, ev0, torch.cuda.current_stream(), parts=(args.side,))))
@@ -431,6 +435,21 @@ def eloc_only(args, w, sig, theta, prec):
         ctx.local_energy(s, out=e, n_nbr=False)
     rc, _ = ctx.sync_status()
     print(json.dumps({"eloc_only": w.name, "batch": w.batch, "precision": prec, "status": rc}))
+    return 0 if rc == 0 else 1
+
+
+def odiff_only(args, w, sig, theta, prec):
+    """O_k launches only, on `w.batch` samples (profiling cases)."""
+    import torch
+    from paper_2108_13830_gb300.binding import VMC
+    ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, prec)
+    ctx.set_params(torch.tensor(theta, device="cuda"))
+    s = torch.tensor(sig, device="cuda")
+    O = torch.empty(w.batch, ctx.n, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        ctx.log_derivs(s, out=O)
+    rc, _ = ctx.sync_status()
+    print(json.dumps({"odiff_only": w.name, "batch": w.batch, "precision": prec, "status": rc}))
     return 0 if rc == 0 else 1
 
 
