@@ -211,3 +211,25 @@ def test_cone_ragged_batch_bitwise():
     big = Ls == 16
     assert np.all(np.isnan(e2[big]))
     np.testing.assert_array_equal(e2[~big], e0.cpu().numpy()[~big])
+
+
+def test_launch_timing_records_the_light_cone_launches():
+    """vmc_set_launch_timing: one record per tensor-core launch of the calls
+    made while it is on (here the parent pass and the light-cone pass of one
+    local-energy call), each with a positive duration, in launch order."""
+    w = inputs.Workload("cone_timing", 12, 32, 4, "bf16", 64, index=84)
+    sig, theta = inputs.workload_inputs(w)
+    v = make_ctx(w, theta=theta)
+    s = to_dev(sig)
+    v.local_energy(s)
+    v.set_launch_timing(True)
+    v.local_energy(s)
+    t = v.launch_timings()
+    v.set_launch_timing(False)
+    assert [name for name, _ in t] == ["tc_eloc_kernel<parent pass>", "tc_eloc_kernel<light cone>"]
+    assert all(ms > 0 for _, ms in t)
+    v.set_light_cone(False)
+    v.set_launch_timing(True)
+    v.local_energy(s)
+    t = v.launch_timings()
+    assert [name for name, _ in t] == ["tc_eloc_kernel"]
