@@ -54,7 +54,8 @@ constexpr int NEPI_WARPS = 16;
 constexpr int NEPI = NEPI_WARPS * 32;     // epilogue threads
 constexpr int MMA_WARP = NEPI_WARPS;       // first of the MMA-issuing warps
 constexpr int NMMA = 2;                    // MMA-issuing warps (alternate tiles)
-constexpr int NTHREADS = NEPI + 32 * NMMA;
+constexpr int WGT_WARP = MMA_WARP + NMMA;  // the warp that issues the weight copies
+constexpr int NTHREADS = NEPI + 32 * (NMMA + 1);
 constexpr int MAX_SLOTS = 16;             // configurations per slab
 constexpr int MAX_P = 8;                  // cells per TMEM lane (P C <= 128 accumulator columns)
 constexpr int POOL_PARTS = 16;             // row blocks of a lattice summed separately by the pooling
@@ -148,6 +149,8 @@ struct __align__(16) Ctrl {   // 16-byte size: the arrays placed after it are re
     float pool_lo[MAX_SLOTS][POOL_PARTS];
     int pool_nz[MAX_SLOTS][POOL_PARTS];
     Parent ring[RING];
+    int mma_steps, mma_done;    // weight steps the MMA issuers ran; issuers finished
+    int wpad[2];
 };
 
 static_assert(sizeof(Ctrl) % 16 == 0, "control block size keeps what follows it 16-byte aligned");
@@ -412,16 +415,36 @@ struct Kern {
         m.PS = (p.BUF / (uint32_t)(g.P * CP8 * 16)) * 16u;
     }
 
+    // cone pass: the geometry of layer l for lattice side Ls
+    __device__ __forceinline__ const LayerGeo &cone_geo(int Ls, int l) const
+    {
+        return p.cone_tab ? p.cone_tab[(Ls >> 1) * 17 + l] : p.cone[l];
+    }
+
     // Geometry of layer l of slab s: per layer for the cone pass (from the
     // per-side table over a ragged batch), one for all layers otherwise.
     __device__ __forceinline__ const LayerGeo &lg(int s, int l) const
     {
-        if constexpr (VAR == VAR_CONE) return p.cone_tab ? p.cone_tab[(c.slab[s].L >> 1) * 17 + l] : p.cone[l];
+        if constexpr (VAR == VAR_CONE) return cone_geo(c.slab[s].L, l);
         else return c.slab[s].g;
     }
 
     // first A row (lane 0) of tile t
     __device__ __forceinline__ static int tile_row(const LayerGeo &g, int t) { return g.RW + min(128 * t, g.NRm); }
+
+    // Cone pass, layer l whose next window is wider (g0: layer l, g1: layer
+    // l + 1): the last tile of layer l that must be drained before tile t of
+    // layer l + 1 may start.  That tile reads its grid up to one grid row and
+    // one lane past its own lanes; layer-l output row Y is row Y + 1 of the
+    // next grid, and the epilogue drains the tiles of a layer in order, so
+    // tiles 0 .. dep_tile hold every layer-l row it reads.
+    __device__ __forceinline__ static int dep_tile(const LayerGeo &g0, const LayerGeo &g1, int t)
+    {
+        const int ymax = (tile_row(g1, t) + 128 + g1.RW) / g1.RW;   // last grid row read
+        const int yn = min(ymax - 1, g0.w);                          // last layer-l row needed
+        const int x = (yn + 1) * g0.RW - 1 - g0.RW - 127;           // lanes past tile 0's last
+        return min(x <= 0 ? 0 : (x + 127) / 128, g0.T - 1);
+    }
 
     // ---------------------------------------------------------------- MMA
     // One MMA whose descriptors are given as (low, high) words: the high
@@ -499,22 +522,20 @@ struct Kern {
     // results do not depend on the split.  Both warps wait for the slab and
     // weight barriers; each commits its MMAs of a weight step to w_empty
     // (two arrivals per phase), and warp 0 alone issues the weight copies.
+    //
+    // Cone pass, layer l - 1 -> l with a wider window (a "wavefront"
+    // hand-off): no slab-wide ready barrier; before issuing tile t of layer
+    // l, its issuer waits for the drain of tile dep_tile(t) of layer l - 1
+    // (the epilogue publishes each tile of such a layer as it releases its
+    // accumulator slot, after the copies of the window's ring), so the
+    // first tiles of a layer start while the last ones of the layer before
+    // are still being drained.
     __device__ void mma_role(int mw)
     {
         const int D = p.D, R = p.nslots;
-        int issued[2] = {0, 0}, waited[2] = {0, 0};
-        // weight step `step` (buffer step & 1) holds layer l
-        auto issue_w = [&](long long step, int l) {
-            const int bsel = (int)(step & 1);
-            const uint32_t bytes = (uint32_t)tc_layer_bytes(C, l);
-            mbar_expect_tx(&c.w_full[bsel], bytes);
-            bulk_g2s(smem + bsel * WB, p.wimg + tc_wimg_offset(C, l), bytes, &c.w_full[bsel]);
-            issued[bsel]++;
-        };
-        if (mw == 0) {
-            issue_w(0, 0);
-            issue_w(1, D >= 1 ? 1 : 0);
-        }
+        long long nseq = 0;                 // sequence number of the next tile
+        long long first_prev[2] = {0, 0};   // first tile of slab s's previous layer
+        int Lsnap[2] = {0, 0};
         bool dead[2] = {false, p.S < 2};
         int cnt[2] = {0, 0};
         uint32_t ph_ar[2] = {0, 0};
@@ -529,65 +550,113 @@ struct Kern {
                 bool any = false;
                 for (int s = 0; s < 2 && ok; ++s) {
                     if (dead[s]) continue;
-                    if (l == 0 || cnt[s] > 0) {
+                    const bool wf = VAR == VAR_CONE && l >= 1 && cone_geo(Lsnap[s], l).w > cone_geo(Lsnap[s], l - 1).w;
+                    if (!wf && (l == 0 || cnt[s] > 0)) {
                         if (!wait_bar(&c.act_ready[s], ph_ar[s], 1)) { ok = false; break; }
                         ph_ar[s] ^= 1;
                     }
                     if (l == 0) {
                         cnt[s] = *(volatile int *)&c.slab[s].count;
+                        // the slab's lattice side, read once per fill: this warp
+                        // may still walk the slab's last tiles (issued by the
+                        // other warp) after the epilogue has refilled it
+                        Lsnap[s] = *(volatile int *)&c.slab[s].L;
                         if (cnt[s] == 0) { dead[s] = true; continue; }
                     }
                     if (!any) {
                         const int bsel = (int)(step & 1);
                         if (!wait_bar(&c.w_full[bsel], (uint32_t)((step >> 1) & 1), 2)) { ok = false; break; }
-                        if (mw == 0) waited[bsel]++;
                         any = true;
                     }
                     int T;
-                    if constexpr (VAR == VAR_CONE) {
-                        if (p.cone_tab) {
-                            const int Ls = *(volatile int *)&c.slab[s].L;
-                            T = p.cone_tab[(Ls >> 1) * 17 + l].T;
-                        } else {
-                            T = p.cone[l].T;
-                        }
-                    } else {
-                        T = *(volatile int *)&c.slab[s].g.T;
-                    }
+                    if constexpr (VAR == VAR_CONE) T = cone_geo(Lsnap[s], l).T;
+                    else T = *(volatile int *)&c.slab[s].g.T;
+                    const long long fprev = first_prev[s];
+                    first_prev[s] = nseq;
                     for (int t = 0; t < T; ++t) {
                         const int slot = nslot;
                         const uint32_t use_par = npar;
                         const bool mine = (nwarp == mw);
+                        const long long n = nseq++;
                         if (++nslot == R) { nslot = 0; npar ^= 1u; }
                         if (++nwarp == NMMA) nwarp = 0;
                         if (!mine) continue;
                         if (!wait_bar(&c.t_empty[slot], use_par ^ 1u, 3)) { ok = false; break; }
+                        if (wf) {
+                            // the drain of tile nd (and, tiles draining in order,
+                            // of every tile before it).  Tile n - R is drained (the
+                            // wait above), so nd's slot has finished its use before
+                            // nd; a tile R or more back is waited for through a later
+                            // one, whose slot is not reused before tile n: the
+                            // parity then names exactly the phase of nd's use
+                            long long nd = fprev + dep_tile(cone_geo(Lsnap[s], l - 1), cone_geo(Lsnap[s], l), t);
+                            if (n - nd >= R) nd = n - R + 1;
+                            if (!wait_bar(&c.t_empty[(int)(nd % R)], (uint32_t)((nd / R) & 1), 8)) { ok = false; break; }
+                        }
                         tc_fence_after();
                         issue_tile(s, l, t, (int)(step & 1), tmem + (uint32_t)(slot * p.slotc));
                         umma_commit(&c.t_full[slot]);
                     }
                 }
                 if (!ok || !any) break;
+                // the step's weight buffer is free once these MMAs complete
                 umma_commit(&c.w_empty[step & 1]);
-                if (step >= 1 && mw == 0) {
-                    if (!wait_bar(&c.w_empty[(step - 1) & 1], (uint32_t)(((step - 1) >> 1) & 1), 4)) { ok = false; break; }
-                    issue_w(step + 1, l == D ? 0 : l + 1);
-                }
                 ++step;
             }
         }
-        // drain: every weight copy issued and every MMA issued must finish
+        // tell the weight warp how many steps ran, then drain every MMA issued
+        atomicMax(&c.mma_steps, (int)step);
+        __threadfence_block();
+        atomicAdd(&c.mma_done, 1);
         const long long cb = p.budget_ns > 1000000000LL ? p.budget_ns : 1000000000LL;
         int dummy_abort = 0;
-        for (int bsel = 0; bsel < 2; ++bsel)
-            while (waited[bsel] < issued[bsel]) {
-                if (!mbar_wait_bounded(&c.w_full[bsel], (uint32_t)(waited[bsel] & 1), &dummy_abort, cb,
-                                       &p.status->flags, &p.status->timeout_site, 5))
-                    break;
-                waited[bsel]++;
-            }
         umma_commit(&c.drain[mw]);
         mbar_wait_bounded(&c.drain[mw], 0, &dummy_abort, cb, &p.status->flags, &p.status->timeout_site, 6);
+    }
+
+    // Weight copies (one lane of warp WGT_WARP).  Weight step st holds layer
+    // st mod (D + 1) (the issuers run every layer of every slab fill) in
+    // buffer st & 1; the copy for step st goes out as soon as the MMAs of
+    // step st - 2, the last readers of that buffer, have completed (both
+    // issuers commit each step to w_empty), independently of where either
+    // issuer is in its walk.  The warp ends once both issuers have finished
+    // and no step that ran is left, after every copy it issued has landed.
+    __device__ void weight_role()
+    {
+        const int D = p.D;
+        auto issue = [&](long long st) {
+            const int b = (int)(st & 1), l = (int)(st % (D + 1));
+            const uint32_t bytes = (uint32_t)tc_layer_bytes(C, l);
+            mbar_expect_tx(&c.w_full[b], bytes);
+            bulk_g2s(smem + b * WB, p.wimg + tc_wimg_offset(C, l), bytes, &c.w_full[b]);
+        };
+        issue(0);
+        issue(1);
+        long long st = 2;
+        uint64_t t0 = global_timer_ns();
+        for (;;) {
+            if (mbar_try_wait(&c.w_empty[st & 1], (uint32_t)(((st - 2) >> 1) & 1))) {
+                issue(st);
+                ++st;
+                t0 = global_timer_ns();
+                continue;
+            }
+            if (*(volatile int *)&c.mma_done == NMMA && st - 2 >= *(volatile int *)&c.mma_steps) break;
+            if (*(volatile int *)&c.abort) break;
+            if ((long long)(global_timer_ns() - t0) > p.budget_ns) {
+                c.abort = 1;
+                atomicOr(&p.status->flags, VMC_STATUS_TIMEOUT);
+                p.status->timeout_site = 4;
+                break;
+            }
+        }
+        // the copies of the last two steps (one per buffer, each its buffer's
+        // latest phase) may not have been waited for by an issuer
+        const long long cb = p.budget_ns > 1000000000LL ? p.budget_ns : 1000000000LL;
+        int dummy_abort = 0;
+        for (long long q = st - 2; q < st; ++q)
+            mbar_wait_bounded(&c.w_full[q & 1], (uint32_t)((q >> 1) & 1), &dummy_abort, cb, &p.status->flags,
+                              &p.status->timeout_site, 5);
     }
 
     // ---------------------------------------------------------------- epilogue
@@ -735,8 +804,10 @@ struct Kern {
 
     // One tile: load the thread's NM chunks under one wait, start clearing
     // them, put the values, and release the slot once the clearing stores
-    // have completed.
-    template <bool POOL>
+    // have completed.  PUB (a cone layer whose window grows): the release
+    // also publishes the tile's activations to the next layer's MMAs, after
+    // the copies of the window's ring (issued before the layer's first tile).
+    template <bool POOL, bool PUB>
     __device__ __forceinline__ void epi_tile(int t, int slot, int tid, const TileCtx &k, bool ok, float *partF,
                                              int *partI)
     {
@@ -758,6 +829,10 @@ struct Kern {
             if (wq * 32 + 31 >= ov) put_chunks<0, NM, POOL>(v, g4, r, Y, rX, Yh, wq * 32 + lane >= ov, k, partF, partI);
             __syncwarp();
             tmem_wait_st();
+        }
+        if constexpr (PUB) {
+            if (t == 0) cp_async_wait_all();
+            fence_proxy_async_smem();
         }
         tc_fence_before();
         __syncwarp();
@@ -966,26 +1041,39 @@ struct Kern {
         const int L = m.L, N = L * L, count = m.count;
         const int w = lg(s, l).w, W4 = w + 4, RWn = lg(s, l + 1).RW;
         const int per = 8 * w + 16;   // ring cells per window
-        const uint32_t out = smem_u32(act_buf(s, l & 1));
+        // one thread per ring cell (consecutive threads: consecutive cells of
+        // a ring row, so the parent-store reads coalesce), its CP8 channel
+        // planes in turn; divisions by per and W4 (< 2^10, operands < 2^16)
+        // as multiply-high
+        const uint32_t mper = udiv_magic((uint32_t)per), mW4 = udiv_magic((uint32_t)W4);
+        const uint32_t out = smem_u32(act_buf(s, l & 1)) + 16u;
         const uint32_t PS = m.PS;
-        const long long lay = (long long)l * CP8 * N;
-        for (int it = tid; it < count * per * CP8; it += NEPI) {
-            const int g = it % CP8;
-            const int rest = it / CP8;
-            const int j = rest / per;
-            int e = rest - j * per;
+        const uint8_t *lay = p.act_store + (long long)l * CP8 * N * 16;
+        for (int it = tid; it < count * per; it += NEPI) {
+            const int j = udiv(it, mper);
+            int e = it - j * per;
             int Xp, Yp;
-            if (e < 2 * W4) { Yp = e / W4; Xp = e - Yp * W4; }
-            else if (e < 4 * W4) { e -= 2 * W4; Yp = w + 2 + e / W4; Xp = e - (Yp - w - 2) * W4; }
-            else { e -= 4 * W4; Yp = 2 + (e >> 2); const int cc = e & 3; Xp = cc < 2 ? cc : w + cc; }
+            if (e < 4 * W4) {
+                // two rows above the window, then two below
+                const int r = udiv(e, mW4);
+                Xp = e - r * W4;
+                Yp = r < 2 ? r : w + r;
+            } else {
+                // the two columns either side of rows 2 .. w + 1
+                e -= 4 * W4;
+                Yp = 2 + (e >> 2);
+                const int cc = e & 3;
+                Xp = cc < 2 ? cc : w + cc;
+            }
             int x = (int)m.ox[j] - l - 2 + Xp, y = (int)m.oy[j] - l - 2 + Yp;
             x += (x < 0) ? L : 0; x += (x < 0) ? L : 0; x -= (x >= L) ? L : 0;
             y += (y < 0) ? L : 0; y += (y < 0) ? L : 0; y -= (y >= L) ? L : 0;
-            const uint8_t *src = p.act_store + (long long)m.pb[j] * p.store_stride + (lay + (long long)g * N + y * L + x) * 16;
+            const uint8_t *src = lay + (long long)m.pb[j] * p.store_stride + (long long)(y * L + x) * 16;
             const int Xg = j * W4 + Xp;
             const int qn = Xg / P;
-            const uint32_t dst = out + (uint32_t)(((Xg - qn * P) * CP8 + g)) * PS + (uint32_t)(Yp * RWn + qn + 1) * 16u;
-            cp_async16(dst, src);
+            const uint32_t dst = out + (uint32_t)((Xg - qn * P) * CP8) * PS + (uint32_t)(Yp * RWn + qn) * 16u;
+#pragma unroll
+            for (int g = 0; g < CP8; ++g) cp_async16(dst + (uint32_t)g * PS, src + (long long)g * N * 16);
         }
     }
 
@@ -1171,12 +1259,12 @@ struct Kern {
     }
 
     // one (slab, layer) of tiles
-    template <bool POOL>
+    template <bool POOL, bool PUB>
     __device__ __forceinline__ void run_tiles(int T, int &slot, uint32_t &use_par, int tid, const TileCtx &k,
                                               float *partF, int *partI)
     {
         for (int t = 0; t < T; ++t) {
-            epi_tile<POOL>(t, slot, tid, k, wait_tile(slot, use_par, tid), partF, partI);
+            epi_tile<POOL, PUB>(t, slot, tid, k, wait_tile(slot, use_par, tid), partF, partI);
             if (++slot == p.nslots) { slot = 0; use_par ^= 1u; }
         }
     }
@@ -1204,20 +1292,24 @@ struct Kern {
                     load_tctx(s, l, tid, k);
                     const int T = k.T;
                     if (l < D) {
-                        // cone pass: the next window's ring is copied from the
-                        // parent while the tiles drain
                         if constexpr (VAR == VAR_CONE) {
-                            if (k.grow) ring_fill(s, l, tid);
+                            if (k.grow) {
+                                // the next window's ring is copied from the parent
+                                // while the tiles drain; each tile is published as
+                                // it is released (no slab-wide hand-off)
+                                ring_fill(s, l, tid);
+                                run_tiles<false, true>(T, slot, use_par, tid, k, nullptr, nullptr);
+                                continue;
+                            }
                         }
-                        run_tiles<false>(T, slot, use_par, tid, k, nullptr, nullptr);
-                        if constexpr (VAR == VAR_CONE) cp_async_wait_all();
+                        run_tiles<false, false>(T, slot, use_par, tid, k, nullptr, nullptr);
                         warp_done(s, tid);
                     } else {
                         // pooling partials go to the buffer layer D - 1 read (its MMAs are
                         // done); the layer-D input buffer is still read by later tiles
                         float *partF = reinterpret_cast<float *>(act_buf(s, p.D & 1));
                         int *partI = reinterpret_cast<int *>(partF + CP8 * k.NQ);
-                        run_tiles<true>(T, slot, use_par, tid, k, partF, partI);
+                        run_tiles<true, false>(T, slot, use_par, tid, k, partF, partI);
                         // every warp's partials are in place; a timed-out or
                         // failed CTA returns here, all warps together
                         if (!cta_check(tid, nchk)) return;
@@ -1258,6 +1350,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
         c.cur_parent = -1; c.cur_k = 0; c.cur_nlist = -1; c.cur_L = 0;
         for (int i = 0; i < 2; ++i) { c.slab[i].count = 0; c.slab[i].L = 0; c.slab[i].G = 0; c.slab[i].g.T = 0; }
         c.pending_b = -1; c.no_more = 0; c.ring_head = 0;
+        c.mma_steps = 0; c.mma_done = 0;
         for (int r = 0; r < RING; ++r) c.ring[r].valid = 0;
         mbar_fence_init();
         fence_proxy_async_smem();
@@ -1278,7 +1371,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     tc_fence_after();
     Kern<C, F16, NM, VAR> k(p, smem, c, spins, list, bias_s, c.tmem_base);
     if (warp < MMA_WARP) k.epilogue_role(tid);
-    else if ((tid & 31) == 0) k.mma_role(warp - MMA_WARP);
+    else if (warp < WGT_WARP) { if ((tid & 31) == 0) k.mma_role(warp - MMA_WARP); }
+    else if ((tid & 31) == 0) k.weight_role();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
