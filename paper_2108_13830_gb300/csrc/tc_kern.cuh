@@ -440,10 +440,10 @@ struct Kern {
     // tiles 0 .. dep_tile hold every layer-l row it reads.
     __device__ __forceinline__ static int dep_tile(const LayerGeo &g0, const LayerGeo &g1, int t)
     {
-        const int ymax = (tile_row(g1, t) + 128 + g1.RW) / g1.RW;   // last grid row read
+        const int ymax = udiv(tile_row(g1, t) + 128 + g1.RW, g1.mRW);   // last grid row read
         const int yn = min(ymax - 1, g0.w);                          // last layer-l row needed
-        const int x = (yn + 1) * g0.RW - 1 - g0.RW - 127;           // lanes past tile 0's last
-        return min(x <= 0 ? 0 : (x + 127) / 128, g0.T - 1);
+        const int x = (yn + 1) * g0.RW - 1 - g0.RW - 127;               // lanes past tile 0's last
+        return min(x <= 0 ? 0 : (x + 127) >> 7, g0.T - 1);
     }
 
     // ---------------------------------------------------------------- MMA
@@ -533,8 +533,8 @@ struct Kern {
     __device__ void mma_role(int mw)
     {
         const int D = p.D, R = p.nslots;
-        long long nseq = 0;                 // sequence number of the next tile
-        long long first_prev[2] = {0, 0};   // first tile of slab s's previous layer
+        int nseq = 0;                       // sequence number of the next tile
+        int first_prev[2] = {0, 0};         // first tile of slab s's previous layer
         int Lsnap[2] = {0, 0};
         bool dead[2] = {false, p.S < 2};
         int cnt[2] = {0, 0};
@@ -571,27 +571,35 @@ struct Kern {
                     int T;
                     if constexpr (VAR == VAR_CONE) T = cone_geo(Lsnap[s], l).T;
                     else T = *(volatile int *)&c.slab[s].g.T;
-                    const long long fprev = first_prev[s];
+                    const int fprev = first_prev[s];
                     first_prev[s] = nseq;
+                    const LayerGeo *gp = nullptr, *gc = nullptr;
+                    if constexpr (VAR == VAR_CONE) {
+                        gp = &cone_geo(Lsnap[s], l > 0 ? l - 1 : 0);
+                        gc = &cone_geo(Lsnap[s], l);
+                    }
                     for (int t = 0; t < T; ++t) {
                         const int slot = nslot;
                         const uint32_t use_par = npar;
                         const bool mine = (nwarp == mw);
-                        const long long n = nseq++;
+                        const int n = nseq++;
                         if (++nslot == R) { nslot = 0; npar ^= 1u; }
                         if (++nwarp == NMMA) nwarp = 0;
                         if (!mine) continue;
                         if (!wait_bar(&c.t_empty[slot], use_par ^ 1u, 3)) { ok = false; break; }
                         if (wf) {
-                            // the drain of tile nd (and, tiles draining in order,
-                            // of every tile before it).  Tile n - R is drained (the
-                            // wait above), so nd's slot has finished its use before
-                            // nd; a tile R or more back is waited for through a later
-                            // one, whose slot is not reused before tile n: the
-                            // parity then names exactly the phase of nd's use
-                            long long nd = fprev + dep_tile(cone_geo(Lsnap[s], l - 1), cone_geo(Lsnap[s], l), t);
-                            if (n - nd >= R) nd = n - R + 1;
-                            if (!wait_bar(&c.t_empty[(int)(nd % R)], (uint32_t)((nd / R) & 1), 8)) { ok = false; break; }
+                            // the drain of tile n - back (and, tiles draining in
+                            // order, of every tile before it).  Tile n - R is drained
+                            // (the wait above), so that tile's slot has finished its
+                            // use before it; a tile R or more back is waited for
+                            // through a later one, whose slot is not reused before
+                            // tile n: the parity then names exactly the phase of its
+                            // use.  Its slot and parity follow from tile n's.
+                            const int back = min(n - (fprev + dep_tile(*gp, *gc, t)), R - 1);   // >= 1
+                            int sd = slot - back;
+                            uint32_t pd = use_par;
+                            if (sd < 0) { sd += R; pd ^= 1u; }
+                            if (!wait_bar(&c.t_empty[sd], pd, 8)) { ok = false; break; }
                         }
                         tc_fence_after();
                         issue_tile(s, l, t, (int)(step & 1), tmem + (uint32_t)(slot * p.slotc));
