@@ -162,6 +162,8 @@ static LayerGeo cone_layer(int L, int l, int G, int P, int *rows)
     g.NRm = std::max(g.w * g.RW - 128, 0);
     g.mRW = udiv_magic((uint32_t)g.RW);
     g.mLP = udiv_magic((uint32_t)(g.w + 2));
+    g.mRing = udiv_magic((uint32_t)(8 * g.w + 16));
+    g.mW4 = udiv_magic((uint32_t)(g.w + 4));
     return g;
 }
 

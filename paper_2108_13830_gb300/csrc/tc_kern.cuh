@@ -70,10 +70,13 @@ struct Geo { int G, P, T, PW; };
 // Slab geometry of one layer: the lattice window its outputs cover (w x w
 // cells, w = L for a whole lattice), tiles, grid row width in cells (a
 // multiple of P), lanes per grid row, the start of the last tile past the
-// first (max(w RW - 128, 0)) and the division magics for RW and w + 2.
+// first (max(w RW - 128, 0)) and the division magics for RW and w + 2; for
+// the light-cone pass also those for the next window's ring (8 w + 16
+// cells) and its grid side w + 4.
 struct LayerGeo {
     int w, T, PW, RW, NRm;
     uint32_t mRW, mLP;
+    uint32_t mRing, mW4;
 };
 
 // Kernel variants: the plain forward (log|psi| or E_loc with full forwards
@@ -412,6 +415,8 @@ struct Kern {
         m.g.NRm = max(L * m.g.RW - 128, 0);
         m.g.mRW = udiv_magic((uint32_t)m.g.RW);
         m.g.mLP = udiv_magic((uint32_t)(L + 2));
+        m.g.mRing = 0u;
+        m.g.mW4 = 0u;
         m.PS = (p.BUF / (uint32_t)(g.P * CP8 * 16)) * 16u;
     }
 
@@ -1047,13 +1052,14 @@ struct Kern {
     {
         const SlabMeta &m = c.slab[s];
         const int L = m.L, N = L * L, count = m.count;
-        const int w = lg(s, l).w, W4 = w + 4, RWn = lg(s, l + 1).RW;
+        const LayerGeo &g = lg(s, l);
+        const int w = g.w, W4 = w + 4, RWn = lg(s, l + 1).RW;
         const int per = 8 * w + 16;   // ring cells per window
         // one thread per ring cell (consecutive threads: consecutive cells of
         // a ring row, so the parent-store reads coalesce), its CP8 channel
         // planes in turn; divisions by per and W4 (< 2^10, operands < 2^16)
         // as multiply-high
-        const uint32_t mper = udiv_magic((uint32_t)per), mW4 = udiv_magic((uint32_t)W4);
+        const uint32_t mper = g.mRing, mW4 = g.mW4;
         const uint32_t out = smem_u32(act_buf(s, l & 1)) + 16u;
         const uint32_t PS = m.PS;
         const uint8_t *lay = p.act_store + (long long)l * CP8 * N * 16;
