@@ -233,6 +233,8 @@ def main():
                     help="profiling case: only the O_k (log-derivative) launch, no JSON contract line")
     ap.add_argument("--batch", type=int, default=0, help="override the workload's batch (profiling cases)")
     ap.add_argument("--precision", default="", help="override the tensor-core operand type (bf16 | fp16)")
+    ap.add_argument("--cone-tiles", default="",
+                    help="profiling case with --eloc-only: light-cone tiles as slabs,lane_cells,slab_configs")
     ap.add_argument("--side", default="", choices=("",) + SIDE_PARTS,
                     help="profiling case: one side measurement only, printed as JSON, no contract line")
     args = ap.parse_args()
@@ -429,6 +431,9 @@ def eloc_only(args, w, sig, theta, prec):
     from paper_2108_13830_gb300.binding import VMC
     ctx = VMC(w.L, w.J1, w.J2, w.C, w.D, prec)
     ctx.set_params(torch.tensor(theta, device="cuda"))
+    if args.cone_tiles:
+        S, P, G = (int(x) for x in args.cone_tiles.split(","))
+        ctx.set_cone_tiles(slab_configs=G, slabs=S, lane_cells=P)
     s = torch.tensor(sig, device="cuda")
     e = torch.empty(w.batch, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup + args.steps):
