@@ -815,6 +815,100 @@ struct Kern {
         }
     }
 
+    // The thread's NM chunks when they are channel planes g0 .. g0 + NM - 1
+    // of one cell of the lane (NM divides C/8): the cell's position,
+    // validity and addresses are computed once.  Same stores as put_chunks.
+    template <bool POOL>
+    __device__ __forceinline__ void put_cell(const float (&v)[NM][8], int g4, int r, int Y, int rX, int Yh,
+                                             bool fresh, const TileCtx &k, float *partF, int *partI)
+    {
+        const int L = k.L;
+        const int ic = (g4 * NM) / CP8, g0 = (g4 * NM) % CP8;
+        const int X = P * rX + ic;
+        const int j = udiv(X, k.mLP);
+        const int x = X - j * (L + 2) - 1;
+        const bool valid = (Y >= 1) & (Y <= L) & fresh & (x >= 0) & (x < L) & (j < k.count);
+        const float4 *b4 = reinterpret_cast<const float4 *>(bias_s + k.l * C + g0 * 8);
+        if constexpr (POOL) {
+            int q0 = Y * k.PW + X;
+            if constexpr (VAR == VAR_CONE) {
+                // the last layer's window is the whole lattice seen from its
+                // own origin: file the partials at the cell's lattice position
+                const int jj = j < MAX_SLOTS ? j : 0;
+                const int ls = (L - 4) >> 1;
+                int xl = (int)k.sm->ox[jj] - ls + x, yl = (int)k.sm->oy[jj] - ls + Y - 1;
+                xl += (xl < 0) ? L : 0; xl -= (xl >= L) ? L : 0;
+                yl += (yl < 0) ? L : 0; yl -= (yl >= L) ? L : 0;
+                q0 = (yl + 1) * k.PW + j * (L + 2) + xl + 1;
+            }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const float4 b0 = b4[2 * m], b1 = b4[2 * m + 1];
+                const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+                float sl = 0.f;
+                int neg = 0, zer = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float h = v[m][q] + bb[q];
+                    sl += __log2f(fabsf(h));
+                    neg += (h < 0.f);
+                    zer += (h == 0.f);
+                }
+                const int qc = (g0 + m) * k.NQ + q0;
+                // log2|z| = log2|h| + 1 per channel
+                st_shared_f32_if(valid, smem_u32(partF + qc), sl + 8.0f);
+                st_shared_b32_if(valid, smem_u32(partI + qc), (uint32_t)(neg | (zer << 16)));
+            }
+        } else {
+            // destination of plane g0 (the others follow PS apart) and, for the
+            // circular halo, the cell's copies
+            uint32_t dst0, hdst = 0u;
+            bool grow = false;
+            if constexpr (VAR == VAR_CONE) grow = k.grow != 0;
+            const int hx = (x == 0) ? L : ((x == L - 1) ? -L : 0);
+            const int Yv = Yh < 0 ? Y : Yh;
+            if (grow) {
+                const int Xn = j * (L + 4) + x + 2;
+                const int qn = Xn / P;
+                dst0 = k.out + (uint32_t)((Xn - qn * P) * CP8 + g0) * k.PS + (uint32_t)((Y + 1) * k.RWn + qn + 1) * 16u;
+            } else {
+                dst0 = k.out + (uint32_t)(ic * CP8 + g0) * k.PS + (uint32_t)(r + 1) * 16u;
+                const int X2 = X + hx;
+                const int xr = X2 / P;
+                hdst = k.out + (uint32_t)((X2 - xr * P) * CP8 + g0) * k.PS + (uint32_t)xr * 16u;
+            }
+            const uint32_t rowY = (uint32_t)(Y * k.RW + 1) * 16u, rowV = (uint32_t)(Yv * k.RW + 1) * 16u;
+            const uint32_t rr = (uint32_t)rX * 16u;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const float4 b0 = b4[2 * m], b1 = b4[2 * m + 1];
+                uint32_t w[4];
+                w[0] = silu_pack2<F16>(v[m][0] + b0.x, v[m][1] + b0.y);
+                w[1] = silu_pack2<F16>(v[m][2] + b0.z, v[m][3] + b0.w);
+                w[2] = silu_pack2<F16>(v[m][4] + b1.x, v[m][5] + b1.y);
+                w[3] = silu_pack2<F16>(v[m][6] + b1.z, v[m][7] + b1.w);
+                const uint32_t pm = (uint32_t)m * k.PS;
+                if constexpr (VAR == VAR_STORE) {
+                    // parent pass: the activation also goes to the parent store
+                    if (valid) {
+                        const int jj = j < MAX_SLOTS ? j : 0;
+                        uint8_t *gd = p.act_store + (long long)k.sm->pb[jj] * p.store_stride +
+                                      ((long long)(k.l * CP8 + g0 + m) * (L * L) + (Y - 1) * L + x) * 16;
+                        st_global_v4(gd, w[0], w[1], w[2], w[3]);
+                    }
+                }
+                if (grow) {
+                    st_shared_v4_if(valid, dst0 + pm, w[0], w[1], w[2], w[3]);
+                } else {
+                    st_shared_v4_if(valid, dst0 + pm, w[0], w[1], w[2], w[3]);
+                    st_shared_v4_if(valid & (hx != 0), hdst + pm + rowY, w[0], w[1], w[2], w[3]);
+                    st_shared_v4_if(valid & (Yh >= 0), dst0 + pm + rowV + rr - (uint32_t)(r + 1) * 16u, w[0], w[1], w[2], w[3]);
+                    st_shared_v4_if(valid & (hx != 0) & (Yh >= 0), hdst + pm + rowV, w[0], w[1], w[2], w[3]);
+                }
+            }
+        }
+    }
+
     // One tile: load the thread's NM chunks under one wait, start clearing
     // them, put the values, and release the slot once the clearing stores
     // have completed.  PUB (a cone layer whose window grows): the release
@@ -825,7 +919,10 @@ struct Kern {
                                              int *partI)
     {
         const int warp = tid >> 5, lane = tid & 31, wq = warp & 3, g4 = warp >> 2;
-        const uint32_t ta = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(slot * p.slotc + 8 * g4);
+        // NM dividing C/8: the thread's chunks are consecutive columns (planes
+        // of one cell); otherwise chunks g4 + 4 m
+        constexpr bool SAMECELL = (CP8 % NM) == 0;
+        const uint32_t ta = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)(slot * p.slotc + 8 * (SAMECELL ? g4 * NM : g4));
         const int r = k.RW + min(128 * t, k.NRm) + wq * 32 + lane;
         const int Y = udiv(r, k.mRW);
         const int rX = r - Y * k.RW;
@@ -837,9 +934,15 @@ struct Kern {
         const int ov = (t == k.T - 1) ? 128 * t - k.NRm : 0;
         float v[NM][8];
         if (ok) {
-            tmem_ld_chunks<NM, 32>(ta, v);
-            tmem_zero_chunks_async<NM, 32>(ta);
-            if (wq * 32 + 31 >= ov) put_chunks<0, NM, POOL>(v, g4, r, Y, rX, Yh, wq * 32 + lane >= ov, k, partF, partI);
+            if constexpr (SAMECELL) {
+                tmem_ld_chunks<NM, 8>(ta, v);
+                tmem_zero_chunks_async<NM, 8>(ta);
+                if (wq * 32 + 31 >= ov) put_cell<POOL>(v, g4, r, Y, rX, Yh, wq * 32 + lane >= ov, k, partF, partI);
+            } else {
+                tmem_ld_chunks<NM, 32>(ta, v);
+                tmem_zero_chunks_async<NM, 32>(ta);
+                if (wq * 32 + 31 >= ov) put_chunks<0, NM, POOL>(v, g4, r, Y, rX, Yh, wq * 32 + lane >= ov, k, partF, partI);
+            }
             __syncwarp();
             tmem_wait_st();
         }
