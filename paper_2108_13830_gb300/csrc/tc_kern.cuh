@@ -151,12 +151,15 @@ struct __align__(16) Ctrl {   // 16-byte size: the arrays placed after it are re
     float pool_hi[MAX_SLOTS][POOL_PARTS];     // per-configuration pooling partials (double-float)
     float pool_lo[MAX_SLOTS][POOL_PARTS];
     int pool_nz[MAX_SLOTS][POOL_PARTS];
+    double pool_la[MAX_SLOTS];                // per-configuration log|psi| and sign
+    int pool_sg[MAX_SLOTS];
     Parent ring[RING];
     int mma_steps, mma_done;    // weight steps the MMA issuers ran; issuers finished
     int wpad[2];
 };
 
 static_assert(sizeof(Ctrl) % 16 == 0, "control block size keeps what follows it 16-byte aligned");
+static_assert(MAX_SLOTS <= NEPI_WARPS, "the pooling gives every configuration of a slab its own warp");
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
 
@@ -957,8 +960,10 @@ struct Kern {
 
     // Per-configuration FP64 sums and the per-parent bookkeeping.  Each
     // configuration's lattice is cut into POOL_PARTS blocks of rows; warps
-    // take (configuration, block) tasks, and thread 0 adds the blocks in
-    // order, so the summation order depends on L only, not on the slab.
+    // take (configuration, block) tasks, then warp j adds configuration j's
+    // blocks in a fixed tree, so the summation order depends on L only, not
+    // on the slab; thread 0 applies the configurations to their parents in
+    // slab order.
     __device__ void pool_finish(int s, int tid, const float *partF, const int *partI, int NQ)
     {
         SlabMeta &m = c.slab[s];
@@ -998,19 +1003,35 @@ struct Kern {
             }
         }
         epi_sync();
+        // warp j adds configuration j's blocks (lane = block) in a fixed tree
+        if (warp < count) {
+            const int j = warp;
+            float hi = 0.f, lo = 0.f;
+            int neg = 0, zer = 0;
+            if (lane < POOL_PARTS) {
+                hi = c.pool_hi[j][lane];
+                lo = c.pool_lo[j][lane];
+                neg = c.pool_nz[j][lane] & 0xffff;
+                zer = c.pool_nz[j][lane] >> 16;
+            }
+            for (int o = POOL_PARTS / 2; o > 0; o >>= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, hi, o), ol = __shfl_xor_sync(0xffffffffu, lo, o);
+                df_add(hi, lo, oh);
+                lo += ol;
+                neg += __shfl_xor_sync(0xffffffffu, neg, o);
+                zer += __shfl_xor_sync(0xffffffffu, zer, o);
+            }
+            if (lane == 0) {
+                const double acc = (double)hi + (double)lo;
+                c.pool_la[j] = zer ? -INFINITY : acc * 0.69314718055994530942;
+                c.pool_sg[j] = zer ? 0 : ((neg & 1) ? -1 : 1);
+            }
+        }
+        epi_sync();
         if (tid == 0) {
             for (int j = 0; j < count; ++j) {
-                float hi = 0.f, lo = 0.f;
-                int neg = 0, zer = 0;
-                for (int part = 0; part < POOL_PARTS; ++part) {
-                    df_add(hi, lo, c.pool_hi[j][part]);
-                    lo += c.pool_lo[j][part];
-                    neg += c.pool_nz[j][part] & 0xffff;
-                    zer += c.pool_nz[j][part] >> 16;
-                }
-                const double acc = (double)hi + (double)lo;
-                const double la = zer ? -INFINITY : acc * 0.69314718055994530942;
-                const int sg = zer ? 0 : ((neg & 1) ? -1 : 1);
+                const double la = c.pool_la[j];
+                const int sg = c.pool_sg[j];
                 Parent &P = c.ring[m.parent[j]];
                 if (m.bond[j] < 0) {
                     P.la0 = la;
