@@ -348,7 +348,9 @@ int vmc_autotune(vmc_ctx *ctx, int L, int64_t probe_B, void *stream);
  * returns VMC_ERR_UNSUPPORTED (and keeps the previous choice) when no plan
  * fits; get reports the plan in use (VMC_ERR_UNSUPPORTED where the light
  * cone does not apply).  vmc_autotune(ctx, ctx's L, ...) also times the
- * best-modelled light-cone plans and keeps the fastest. */
+ * best-modelled light-cone plans and keeps the fastest.  The light-cone
+ * pass of vmc_local_energy_ragged takes slabs and lane_cells for its
+ * launch and slab_configs as the upper bound of every side's windows. */
 int vmc_set_cone_tiles(vmc_ctx *ctx, const vmc_tiles *tiles);
 int vmc_get_cone_tiles(const vmc_ctx *ctx, vmc_tiles *tiles);
 

@@ -168,17 +168,27 @@ static LayerGeo cone_layer(int L, int l, int G, int P, int *rows)
 }
 
 // Modelled cycles of one neighbour through every layer with G windows per
-// slab: the MMA cost of each layer's tiles plus a hand-off per slab-layer
-// (the last tile's epilogue and the barrier), shared by the G windows.  With
-// one slab nothing hides the hand-off; with two the other slab's MMAs do.
+// slab, shared by the G windows.  A layer whose windows fit one tile is a
+// strict chain (its MMAs, then its drain, then the next layer's MMAs; two
+// slabs overlap two such chains); a wider layer costs its tiles' epilogue
+// drains (the tile-level hand-off hides its MMAs); every slab pays the
+// pooling and the next fill.  The constants are fitted to measured launch
+// times over C = 16 and 32, L = 8 .. 24, one and two slabs, P = 1 .. 8:
+// the model's pick is within 3 % of the fastest measured choice in each.
 static double cone_cost(int C, int L, int D, int G, int P, int S)
 {
-    double cyc = 0;
-    for (int l = 0; l <= D; ++l) {
+    const double nm = P * C / 32.0;                           // accumulator chunks per epilogue thread
+    const double mma = 312.0 * 3 * (C / 16) * (P + 2);        // one tile's MMAs
+    const double drain = 1070.0 + 1220.0 * nm;                // one tile's epilogue
+    const double chain = mma + drain;                         // a one-tile layer: MMAs, then the drain
+    double cyc = 170.0 + drain;                               // the embedding layer
+    for (int l = 1; l <= D; ++l) {
         int rows;
         const LayerGeo g = cone_layer(L, l, G, P, &rows);
-        cyc += g.T * (l == 0 ? P * mma_cycles(C) : tile_cycles(C, P)) + (S == 1 ? 1800.0 : 300.0);
+        if (g.T == 1) cyc += S == 1 ? chain : std::max(chain / 2, drain);
+        else cyc += g.T * drain + (S == 1 ? 1240.0 : 0.0);
     }
+    cyc += 11900.0 + 680.0 * G;                               // pooling and the next fill
     return cyc / G;
 }
 
@@ -269,17 +279,23 @@ static int make_cone_plan_ragged(const vmc_ctx *ctx, int L_max, Plan *pl, std::v
 {
     const int C = ctx->arch.channels, D = ctx->arch.n_layers_cc;
     if (cone_w(L_max, D) != L_max) return VMC_ERR_UNSUPPORTED;
+    // explicit light-cone tiles: slabs and P for the launch, windows per slab
+    // as every side's upper bound
+    const TileChoice &tc = ctx->cone_tiles;
+    const int gmax = tc.slab_configs ? std::min(tc.slab_configs, MAX_SLOTS) : MAX_SLOTS;
     double best = 1e300;
     int bS = 0, bP = 0;
     for (int S = 1; S <= 2; ++S) {
+        if (tc.slabs && S != tc.slabs) continue;
         const uint32_t buf = buf_bytes(C, S, L_max, D);
         for (int P = 1; P <= MAX_P; ++P) {
             if (!p_allowed(C, P)) continue;
+            if (tc.lane_cells && P != tc.lane_cells) continue;
             double tot = 0;
             bool ok = true;
             for (int L = 4; L <= L_max && ok; L += 2) {
                 double bl = 1e300;
-                for (int G = 1; G <= MAX_SLOTS; ++G) {
+                for (int G = 1; G <= gmax; ++G) {
                     int rows_max = 0;
                     for (int l = 0; l <= D; ++l) {
                         int rows;
@@ -305,7 +321,7 @@ static int make_cone_plan_ragged(const vmc_ctx *ctx, int L_max, Plan *pl, std::v
     for (int L = 4; L <= L_max; L += 2) {
         double bl = 1e300;
         int bG = 0;
-        for (int G = 1; G <= MAX_SLOTS; ++G) {
+        for (int G = 1; G <= gmax; ++G) {
             int rows_max = 0;
             for (int l = 0; l <= D; ++l) {
                 int rows;

@@ -233,3 +233,22 @@ def test_launch_timing_records_the_light_cone_launches():
     v.local_energy(s)
     t = v.launch_timings()
     assert [name for name, _ in t] == ["tc_eloc_kernel"]
+
+
+@pytest.mark.parametrize("S,P", [(1, 4), (2, 2), (1, 8)])
+def test_cone_ragged_explicit_tiles(S, P):
+    """vmc_set_cone_tiles applies to the ragged light-cone launch (slabs and
+    P for the launch, each side's windows per slab from the cost model):
+    every choice gives the plain ragged evaluation's results bit for bit."""
+    w = inputs.Workload("cone_ragt", 16, 16, 6, "fp16", 64, kind="ragged", Ls=(6, 8, 12, 16), index=85)
+    packed, offs, Ls, theta = inputs.ragged_inputs(w)
+    v = make_ctx(w, theta=theta, L=16)
+    pk, of, Lt = to_dev(packed), to_dev(offs), to_dev(Ls)
+    v.set_light_cone(False)
+    e0, n0 = v.local_energy_ragged(pk, of, Lt, 16)
+    v.set_light_cone(True)
+    v.set_cone_tiles(slabs=S, lane_cells=P)
+    e1, n1 = v.local_energy_ragged(pk, of, Lt, 16)
+    assert v.sync_status() == (VMC_OK, 0)
+    np.testing.assert_array_equal(n1.cpu().numpy(), n0.cpu().numpy())
+    np.testing.assert_array_equal(e1.cpu().numpy(), e0.cpu().numpy())
