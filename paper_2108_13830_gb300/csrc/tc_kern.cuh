@@ -156,6 +156,8 @@ struct __align__(16) Ctrl {   // 16-byte size: the arrays placed after it are re
     Parent ring[RING];
     int mma_steps, mma_done;    // weight steps the MMA issuers ran; issuers finished
     int wpad[2];
+    uint64_t staged;            // one-slab light-cone pass: a staged fill is ready
+    SlabMeta stage;             // the staged fill
 };
 
 static_assert(sizeof(Ctrl) % 16 == 0, "control block size keeps what follows it 16-byte aligned");
@@ -630,49 +632,70 @@ struct Kern {
         mbar_wait_bounded(&c.drain[mw], 0, &dummy_abort, cb, &p.status->flags, &p.status->timeout_site, 6);
     }
 
-    // Weight copies (one lane of warp WGT_WARP).  Weight step st holds layer
+    // Weight copies (lane 0 of warp WGT_WARP).  Weight step st holds layer
     // st mod (D + 1) (the issuers run every layer of every slab fill) in
     // buffer st & 1; the copy for step st goes out as soon as the MMAs of
     // step st - 2, the last readers of that buffer, have completed (both
     // issuers commit each step to w_empty), independently of where either
-    // issuer is in its walk.  The warp ends once both issuers have finished
-    // and no step that ran is left, after every copy it issued has landed.
-    __device__ void weight_role()
+    // issuer is in its walk.  With producer_fill() the whole warp also
+    // stages each slab fill when the previous slab's last layer has
+    // completed.  The warp ends once both issuers have finished and no step
+    // that ran is left, after every copy it issued has landed.
+    __device__ void weight_role(int lane)
     {
         const int D = p.D;
+        const bool prod = producer_fill();
         auto issue = [&](long long st) {
             const int b = (int)(st & 1), l = (int)(st % (D + 1));
             const uint32_t bytes = (uint32_t)tc_layer_bytes(C, l);
             mbar_expect_tx(&c.w_full[b], bytes);
             bulk_g2s(smem + b * WB, p.wimg + tc_wimg_offset(C, l), bytes, &c.w_full[b]);
         };
-        issue(0);
-        issue(1);
+        // the first fill, staged before the first weights (both are needed
+        // before the first MMA)
+        bool more = prod ? stage_fill(lane) : false;
+        if (lane == 0) {
+            issue(0);
+            issue(1);
+        }
         long long st = 2;
         uint64_t t0 = global_timer_ns();
         for (;;) {
-            if (mbar_try_wait(&c.w_empty[st & 1], (uint32_t)(((st - 2) >> 1) & 1))) {
-                issue(st);
-                ++st;
-                t0 = global_timer_ns();
-                continue;
+            int done = 0, stop = 0;
+            if (lane == 0) {
+                if (mbar_try_wait(&c.w_empty[st & 1], (uint32_t)(((st - 2) >> 1) & 1))) {
+                    done = 1;
+                } else if (*(volatile int *)&c.mma_done == NMMA && st - 2 >= *(volatile int *)&c.mma_steps) {
+                    stop = 1;
+                } else if (*(volatile int *)&c.abort) {
+                    stop = 1;
+                } else if ((long long)(global_timer_ns() - t0) > p.budget_ns) {
+                    c.abort = 1;
+                    atomicOr(&p.status->flags, VMC_STATUS_TIMEOUT);
+                    p.status->timeout_site = 4;
+                    stop = 1;
+                }
             }
-            if (*(volatile int *)&c.mma_done == NMMA && st - 2 >= *(volatile int *)&c.mma_steps) break;
-            if (*(volatile int *)&c.abort) break;
-            if ((long long)(global_timer_ns() - t0) > p.budget_ns) {
-                c.abort = 1;
-                atomicOr(&p.status->flags, VMC_STATUS_TIMEOUT);
-                p.status->timeout_site = 4;
-                break;
-            }
+            done = __shfl_sync(0xffffffffu, done, 0);
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (stop) break;
+            if (!done) continue;
+            if (lane == 0) issue(st);
+            // step st - 2 was a slab's last layer: its input buffer is free and
+            // the next fill can be staged
+            if (more && (st - 2) % (D + 1) == D) more = stage_fill(lane);
+            ++st;
+            if (lane == 0) t0 = global_timer_ns();
         }
         // the copies of the last two steps (one per buffer, each its buffer's
         // latest phase) may not have been waited for by an issuer
-        const long long cb = p.budget_ns > 1000000000LL ? p.budget_ns : 1000000000LL;
-        int dummy_abort = 0;
-        for (long long q = st - 2; q < st; ++q)
-            mbar_wait_bounded(&c.w_full[q & 1], (uint32_t)((q >> 1) & 1), &dummy_abort, cb, &p.status->flags,
-                              &p.status->timeout_site, 5);
+        if (lane == 0) {
+            const long long cb = p.budget_ns > 1000000000LL ? p.budget_ns : 1000000000LL;
+            int dummy_abort = 0;
+            for (long long q = st - 2; q < st; ++q)
+                mbar_wait_bounded(&c.w_full[q & 1], (uint32_t)((q >> 1) & 1), &dummy_abort, cb, &p.status->flags,
+                                  &p.status->timeout_site, 5);
+        }
     }
 
     // ---------------------------------------------------------------- epilogue
@@ -1121,19 +1144,19 @@ struct Kern {
     }
 
     // Cone pass, embedding layer: the im2col rows of the w0 x w0 window of
-    // each neighbour sigma' of slots [first, first + n), the window's cell
-    // (X, Y), 1 <= X, Y <= w0, being lattice site (ox + X - 1, oy + Y - 1)
-    // mod L; windows lie side by side, w0 + 2 cells apart.
-    __device__ void build_rows_cone(int s, int first, int n, int tid)
+    // each neighbour sigma' of slots [first, first + n) of meta m (filling
+    // slab s), the window's cell (X, Y), 1 <= X, Y <= w0, being lattice site
+    // (ox + X - 1, oy + Y - 1) mod L; windows lie side by side, w0 + 2 cells
+    // apart.  Threads t0, t0 + nthr, ... of the filling group.
+    __device__ void build_rows_cone(const SlabMeta &m, int s, int first, int n, int t0, int nthr)
     {
-        const SlabMeta &m = c.slab[s];
         const int L = m.L;
-        const LayerGeo &g0 = lg(s, 0);
+        const LayerGeo &g0 = cone_geo(L, 0);
         const int w0 = g0.w, PW = g0.PW;
         const uint32_t a0 = smem_u32(act_buf(s, 1));
         const uint32_t PS = m.PS;
         const uint32_t up = F16 ? 0x3C00u : 0x3F80u, dn = F16 ? 0xBC00u : 0xBF80u;
-        for (int it = tid; it < n * w0 * w0; it += NEPI) {
+        for (int it = t0; it < n * w0 * w0; it += nthr) {
             const int jrel = it / (w0 * w0), cell = it - jrel * (w0 * w0);
             const int Y = cell / w0 + 1, X = cell - (Y - 1) * w0 + 1;
             const int jj = first + jrel;
@@ -1215,6 +1238,134 @@ struct Kern {
         }
     }
 
+    // The configuration stream's next step for meta m (one thread decides):
+    // 0 = configurations of the current parent taken into m (c.seg_first,
+    // c.seg_n), 1 = a new parent c.new_b of side c.new_L is to be loaded,
+    // 2 = stop (the slab is full, no work is left, or the CTA aborts).
+    __device__ int next_step(SlabMeta &m, bool first)
+    {
+        if (first) { m.count = 0; m.L = 0; }
+        int act = 2;
+        if (c.abort) {
+            act = 2;   // stop filling; the next abort check ends the epilogue
+        } else if (c.cur_parent >= 0 && c.cur_k <= c.cur_nlist) {
+            act = 0;
+        } else {
+            while (!c.no_more) {
+                long long b = c.pending_b;
+                c.pending_b = -1;
+                if (b < 0) {
+                    // next work item; a ragged batch is walked in the
+                    // order of `order` (largest lattices first)
+                    const long long idx = (long long)atomicAdd(p.counter, 1);
+                    if (idx >= p.B) { c.no_more = 1; break; }
+                    b = p.order ? p.order[idx] : idx;
+                }
+                const int Lb = p.Ls ? p.Ls[b] : p.L_uniform;
+                if ((Lb & 1) || Lb < 4 || Lb > p.L_max || p.geo[Lb >> 1].G == 0) {
+                    p.out_a[b] = nan_d();
+                    if (p.mode == 0) p.out_sign[b] = 0;
+                    if (p.n_nbr) p.n_nbr[b] = 0;
+                    atomicOr(&p.status->flags, VMC_STATUS_BADARG);
+                    continue;
+                }
+                if (m.count > 0 && Lb != m.L) { c.pending_b = b; break; }
+                c.new_b = b;
+                c.new_L = Lb;
+                act = 1;
+                break;
+            }
+        }
+        if (act == 0) {
+            // the slab takes the geometry of the lattice now at the cursor
+            // (a new parent, or the rest of the previous fill's parent)
+            if (m.count == 0) set_geometry(m, c.cur_L, p.geo[c.cur_L >> 1]);
+            if (m.G < 1 || m.G > MAX_SLOTS || m.P != P) {
+                c.abort = 1;
+                atomicOr(&p.status->flags, VMC_STATUS_INTERNAL);
+                m.G = 1;
+            }
+            const int n_take = min(m.G - m.count, c.cur_nlist + 1 - c.cur_k);
+            for (int i = 0; i < n_take; ++i) {
+                const int kk = c.cur_k + i;
+                const int jj = m.count + i;
+                m.parent[jj] = c.cur_parent;
+                m.bond[jj] = (kk == 0) ? -1 : (int)list[kk - 1];
+                if constexpr (VAR != VAR_PLAIN) m.pb[jj] = (int)c.ring[c.cur_parent].b;
+                if constexpr (VAR == VAR_CONE) {
+                    // origin of the layer-0 window: one cell up and left of
+                    // the pair's top-left site (the down-left pair's
+                    // top-left site is its partner's column)
+                    const int L = c.cur_L, k2 = m.bond[jj], si = k2 >> 2, t = k2 & 3;
+                    const int y = si / L, x = si - y * L;
+                    int ox = (t == 3 ? x - 1 : x) - 1, oy = y - 1;
+                    ox += (ox < 0) ? L : 0; ox += (ox < 0) ? L : 0;
+                    oy += (oy < 0) ? L : 0;
+                    m.ox[jj] = (int8_t)ox;
+                    m.oy[jj] = (int8_t)oy;
+                }
+            }
+            c.seg_first = m.count;
+            c.seg_n = n_take;
+            m.count += n_take;
+            c.cur_k += n_take;
+        }
+        return act;
+    }
+
+    // A new parent c.new_b: its spins (threads t, t + nthr, ...), then, in
+    // the filling group's first warp (`inwarp`), its bond list (or Marshall
+    // parity) and, from the group's thread 0, its ring entry.  `sync` is the
+    // group's barrier.
+    template <class Sync>
+    __device__ void load_parent(int t, int nthr, bool inwarp, Sync sync)
+    {
+        const int Lb = c.new_L;
+        const long long b = c.new_b;
+        const int8_t *sig = p.sigma + (p.offs ? p.offs[b] : b * (long long)Lb * Lb);
+        for (int i = t; i < Lb * Lb; i += nthr) spins[i] = sig[i];
+        sync();
+        if (inwarp) {
+            int a1 = 0, a2 = 0, cnt = 0, par = 0;
+            if (p.mode == 1) cnt = build_bond_list_warp(spins, Lb, list, &a1, &a2);
+            else par = marshall_parity_warp(spins, Lb);
+            __syncwarp();
+            if (t == 0) {
+                const int r = c.ring_head;
+                c.ring_head = (r + 1) % RING;
+                Parent &Q = c.ring[r];
+                if (*(volatile int *)&Q.valid) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); }
+                Q.b = b;
+                Q.diag = (p.mode == 1) ? diag_energy(Lb, a1, a2, p.J1, p.J2) : 0.0;
+                Q.la0 = 0.0; Q.acc = 0.0; Q.sg0 = 0;
+                Q.nlist = cnt;
+                Q.remaining = 1 + cnt;
+                Q.mpar = par;
+                Q.valid = 1;
+                Q.L = Lb;
+                c.cur_parent = r;
+                c.cur_k = 0;
+                c.cur_nlist = cnt;
+                c.cur_L = Lb;
+                if constexpr (VAR == VAR_CONE) {
+                    // the parent's amplitude comes from the parent pass;
+                    // only its neighbours enter slabs
+                    Q.la0 = p.par_la[b];
+                    Q.sg0 = (int)p.par_sg[b];
+                    Q.remaining = cnt;
+                    c.cur_k = 1;
+                    if (cnt == 0 || Q.sg0 == 0 || !isfinite(Q.la0)) {
+                        // nothing to evaluate (no exchange neighbour), or a
+                        // parent whose E_loc is NaN whatever they give
+                        finish_parent(Q);
+                        Q.valid = 0;
+                        c.cur_parent = -1;
+                    }
+                }
+            }
+        }
+    }
+
     // Fill slab s with the next configurations of the stream; returns count.
     // Thread 0 decides each step (next parent, or more neighbours of the
     // current one) and takes configurations into the slab in the same
@@ -1227,129 +1378,17 @@ struct Kern {
         SlabMeta &m = c.slab[s];
         bool first = true;
         for (;;) {
-            if (tid == 0) {
-                if (first) { m.count = 0; m.L = 0; }
-                int act = 2;
-                if (c.abort) {
-                    act = 2;   // stop filling; the caller's next abort check ends the epilogue
-                } else if (c.cur_parent >= 0 && c.cur_k <= c.cur_nlist) {
-                    act = 0;
-                } else {
-                    while (!c.no_more) {
-                        long long b = c.pending_b;
-                        c.pending_b = -1;
-                        if (b < 0) {
-                            // next work item; a ragged batch is walked in the
-                            // order of `order` (largest lattices first)
-                            const long long idx = (long long)atomicAdd(p.counter, 1);
-                            if (idx >= p.B) { c.no_more = 1; break; }
-                            b = p.order ? p.order[idx] : idx;
-                        }
-                        const int Lb = p.Ls ? p.Ls[b] : p.L_uniform;
-                        if ((Lb & 1) || Lb < 4 || Lb > p.L_max || p.geo[Lb >> 1].G == 0) {
-                            p.out_a[b] = nan_d();
-                            if (p.mode == 0) p.out_sign[b] = 0;
-                            if (p.n_nbr) p.n_nbr[b] = 0;
-                            atomicOr(&p.status->flags, VMC_STATUS_BADARG);
-                            continue;
-                        }
-                        if (m.count > 0 && Lb != m.L) { c.pending_b = b; break; }
-                        c.new_b = b;
-                        c.new_L = Lb;
-                        act = 1;
-                        break;
-                    }
-                }
-                if (act == 0) {
-                    // the slab takes the geometry of the lattice now at the cursor
-                    // (a new parent, or the rest of the previous fill's parent)
-                    if (m.count == 0) set_geometry(m, c.cur_L, p.geo[c.cur_L >> 1]);
-                    if (m.G < 1 || m.G > MAX_SLOTS || m.P != P) {
-                        c.abort = 1;
-                        atomicOr(&p.status->flags, VMC_STATUS_INTERNAL);
-                        m.G = 1;
-                    }
-                    const int n_take = min(m.G - m.count, c.cur_nlist + 1 - c.cur_k);
-                    for (int i = 0; i < n_take; ++i) {
-                        const int kk = c.cur_k + i;
-                        const int jj = m.count + i;
-                        m.parent[jj] = c.cur_parent;
-                        m.bond[jj] = (kk == 0) ? -1 : (int)list[kk - 1];
-                        if constexpr (VAR != VAR_PLAIN) m.pb[jj] = (int)c.ring[c.cur_parent].b;
-                        if constexpr (VAR == VAR_CONE) {
-                            // origin of the layer-0 window: one cell up and left of
-                            // the pair's top-left site (the down-left pair's
-                            // top-left site is its partner's column)
-                            const int L = c.cur_L, k2 = m.bond[jj], si = k2 >> 2, t = k2 & 3;
-                            const int y = si / L, x = si - y * L;
-                            int ox = (t == 3 ? x - 1 : x) - 1, oy = y - 1;
-                            ox += (ox < 0) ? L : 0; ox += (ox < 0) ? L : 0;
-                            oy += (oy < 0) ? L : 0;
-                            m.ox[jj] = (int8_t)ox;
-                            m.oy[jj] = (int8_t)oy;
-                        }
-                    }
-                    c.seg_first = m.count;
-                    c.seg_n = n_take;
-                    m.count += n_take;
-                    c.cur_k += n_take;
-                }
-                c.action = act;
-            }
+            if (tid == 0) c.action = next_step(m, first);
             first = false;
             epi_sync();
             const int act = c.action;
             if (act == 2) break;
             if (act == 1) {
-                // a new parent: its spins, then (warp 0) its bond list and ring entry
-                const int Lb = c.new_L;
-                const long long b = c.new_b;
-                const int8_t *sig = p.sigma + (p.offs ? p.offs[b] : b * (long long)Lb * Lb);
-                for (int i = tid; i < Lb * Lb; i += NEPI) spins[i] = sig[i];
-                epi_sync();
-                if (tid < 32) {
-                    int a1 = 0, a2 = 0, cnt = 0, par = 0;
-                    if (p.mode == 1) cnt = build_bond_list_warp(spins, Lb, list, &a1, &a2);
-                    else par = marshall_parity_warp(spins, Lb);
-                    __syncwarp();
-                    if (tid == 0) {
-                        const int r = c.ring_head;
-                        c.ring_head = (r + 1) % RING;
-                        Parent &Q = c.ring[r];
-                        if (Q.valid) { c.abort = 1; atomicOr(&p.status->flags, VMC_STATUS_INTERNAL); }
-                        Q.b = b;
-                        Q.diag = (p.mode == 1) ? diag_energy(Lb, a1, a2, p.J1, p.J2) : 0.0;
-                        Q.la0 = 0.0; Q.acc = 0.0; Q.sg0 = 0;
-                        Q.nlist = cnt;
-                        Q.remaining = 1 + cnt;
-                        Q.mpar = par;
-                        Q.valid = 1;
-                        Q.L = Lb;
-                        c.cur_parent = r;
-                        c.cur_k = 0;
-                        c.cur_nlist = cnt;
-                        c.cur_L = Lb;
-                        if constexpr (VAR == VAR_CONE) {
-                            // the parent's amplitude comes from the parent pass;
-                            // only its neighbours enter slabs
-                            Q.la0 = p.par_la[b];
-                            Q.sg0 = (int)p.par_sg[b];
-                            Q.remaining = cnt;
-                            c.cur_k = 1;
-                            if (cnt == 0 || Q.sg0 == 0 || !isfinite(Q.la0)) {
-                                // nothing to evaluate (no exchange neighbour), or a
-                                // parent whose E_loc is NaN whatever they give
-                                finish_parent(Q);
-                                Q.valid = 0;
-                                c.cur_parent = -1;
-                            }
-                        }
-                    }
-                }
+                load_parent(tid, NEPI, tid < 32, [] { epi_sync(); });
                 continue;   // thread 0 takes its configurations next; warp 0's list is
                             // complete before thread 0 reads it (same warp, after __syncwarp)
             }
-            if constexpr (VAR == VAR_CONE) build_rows_cone(s, c.seg_first, c.seg_n, tid);
+            if constexpr (VAR == VAR_CONE) build_rows_cone(m, s, c.seg_first, c.seg_n, tid, NEPI);
             else build_rows(s, c.seg_first, c.seg_n, tid);
             if (m.count >= m.G) break;
             epi_sync();     // build_rows reads m.bond; thread 0 writes it next
@@ -1357,6 +1396,66 @@ struct Kern {
         // cells of no configuration keep whatever the buffer held: they feed
         // only outputs that are dropped
         return m.count;
+    }
+
+    // One-slab light-cone pass with an even number of C -> C layers: the
+    // weight warp stages every slab fill (configurations, new parents, the
+    // embedding layer's im2col into buffer 1, which the last layer reads and
+    // the pooling does not use) as soon as the previous slab's last-layer
+    // MMAs have completed, so the epilogue only copies the staged descriptor
+    // after its pooling.
+    __device__ __forceinline__ bool producer_fill() const
+    {
+        return VAR == VAR_CONE && p.S == 1 && (p.D & 1) == 0;
+    }
+
+    // Weight warp (all lanes): the next fill into c.stage, then the staged
+    // barrier; returns whether it holds configurations.
+    __device__ bool stage_fill(int lane)
+    {
+        SlabMeta &m = c.stage;
+        bool first = true;
+        for (;;) {
+            int act = 2;
+            if (lane == 0) act = next_step(m, first);
+            act = __shfl_sync(0xffffffffu, act, 0);
+            first = false;
+            __syncwarp();
+            if (act == 2) break;
+            if (act == 1) {
+                load_parent(lane, 32, true, [] { __syncwarp(); });
+                __syncwarp();
+                continue;
+            }
+            if constexpr (VAR == VAR_CONE) build_rows_cone(m, 0, c.seg_first, c.seg_n, lane, 32);
+            __syncwarp();
+            if (m.count >= m.G) break;
+        }
+        const int cnt = m.count;
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&c.staged);
+        return cnt > 0;
+    }
+
+    // Epilogue: wait for the staged fill and copy its descriptor into slab
+    // s; returns its count (0 when the CTA has aborted).
+    __device__ int take_stage(int s, int tid, uint32_t &spar, int &nchk)
+    {
+        if ((tid & 31) == 0) wait_bar(&c.staged, spar, 9);
+        __syncwarp();
+        spar ^= 1u;
+        if (!cta_check(tid, nchk)) {
+            if (tid == 0) c.slab[s].count = 0;
+            epi_sync();
+            return 0;
+        }
+        constexpr int NW = (int)(sizeof(SlabMeta) / 4);
+        static_assert(sizeof(SlabMeta) % 4 == 0, "slab descriptor copied as words");
+        for (int i = tid; i < NW; i += NEPI)
+            reinterpret_cast<int *>(&c.slab[s])[i] = reinterpret_cast<const int *>(&c.stage)[i];
+        epi_sync();
+        return c.slab[s].count;
     }
 
     // End of a (slab, layer) for this warp: make its shared-memory writes
@@ -1412,13 +1511,14 @@ struct Kern {
         const int D = p.D;
         bool dead[2] = {false, true};
         int slot = 0;
-        uint32_t use_par = 0;
+        uint32_t use_par = 0, spar = 0;
         int nchk = 0;
+        const bool prod = producer_fill();
         // all layers' biases into shared memory once
         for (int i = tid; i < (D + 1) * C; i += NEPI) bias_s[i] = p.bias32[i];
         epi_sync();
         for (int s = 0; s < p.S; ++s) {
-            const int cnt = fill(s, tid);
+            const int cnt = prod ? take_stage(s, tid, spar, nchk) : fill(s, tid);
             warp_done(s, tid);
             dead[s] = (cnt == 0);
         }
@@ -1452,7 +1552,7 @@ struct Kern {
                         // failed CTA returns here, all warps together
                         if (!cta_check(tid, nchk)) return;
                         pool_finish(s, tid, partF, partI, k.NQ);
-                        const int cnt = fill(s, tid);
+                        const int cnt = prod ? take_stage(s, tid, spar, nchk) : fill(s, tid);
                         warp_done(s, tid);
                         dead[s] = (cnt == 0);
                     }
@@ -1484,6 +1584,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
             mbar_init(&c.t_empty[i], NEPI_WARPS);   // one arrival per epilogue warp
         }
         for (int i = 0; i < NMMA; ++i) mbar_init(&c.drain[i], 1);
+        mbar_init(&c.staged, 1);
         c.abort = 0;
         c.cur_parent = -1; c.cur_k = 0; c.cur_nlist = -1; c.cur_L = 0;
         for (int i = 0; i < 2; ++i) { c.slab[i].count = 0; c.slab[i].L = 0; c.slab[i].G = 0; c.slab[i].g.T = 0; }
@@ -1510,7 +1611,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_eloc_kernel(const __grid_const
     Kern<C, F16, NM, VAR> k(p, smem, c, spins, list, bias_s, c.tmem_base);
     if (warp < MMA_WARP) k.epilogue_role(tid);
     else if (warp < WGT_WARP) { if ((tid & 31) == 0) k.mma_role(warp - MMA_WARP); }
-    else if ((tid & 31) == 0) k.weight_role();
+    else k.weight_role(tid & 31);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
