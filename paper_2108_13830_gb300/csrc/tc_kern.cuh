@@ -30,13 +30,15 @@
 // Warp roles: warps 0-15 (the "epilogue" group) build neighbours, drain
 // TMEM tile by tile (bias, SiLU -> 16-bit into the next padded buffer with
 // the circular halo copies), pool the last layer and keep the per-parent
-// FP64 energy sums; warp 16 allocates TMEM and one lane issues every MMA and
-// the per-layer weight bulk copies (a two-deep ring).  Accumulators live in
-// a ring of TMEM slots (one tile each) with full/empty mbarriers, and two
-// slabs alternate, so the epilogue of one tile overlaps the MMAs of the
-// next.  Every mbarrier wait is bounded by a time budget; on expiry the CTA
-// raises VMC_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM and
-// returns.
+// FP64 energy sums; warps 16 and 17 issue the MMAs of alternate tiles (one
+// lane each; warp 16 also allocates TMEM); warp 18 issues the per-layer
+// weight bulk copies (a two-deep ring) and, in the one-slab light-cone
+// pass, stages every slab fill.  Accumulators live in a ring of TMEM slots
+// (one tile each) with full/empty mbarriers, and two slabs alternate (or,
+// in the light-cone pass, a growing layer is handed to the next tile by
+// tile), so the epilogue of one tile overlaps the MMAs of the next.  Every
+// mbarrier wait is bounded by a time budget; on expiry the CTA raises
+// VMC_ERR_TIMEOUT, drains its own copies and MMAs, frees TMEM and returns.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
