@@ -174,7 +174,8 @@ static LayerGeo cone_layer(int L, int l, int G, int P, int *rows)
 // drains (the tile-level hand-off hides its MMAs); every slab pays the
 // pooling and the next fill.  The constants are fitted to measured launch
 // times over C = 16 and 32, L = 8 .. 24, one and two slabs, P = 1 .. 8:
-// the model's pick is within 3 % of the fastest measured choice in each.
+// the model's pick is within 0-6 % of the fastest measured choice at each
+// size (vmc_autotune times the best-modelled plans).
 static double cone_cost(int C, int L, int D, int G, int P, int S)
 {
     const double nm = P * C / 32.0;                           // accumulator chunks per epilogue thread
