@@ -533,7 +533,8 @@ struct Kern {
     // bound.  Each tile's MMAs come from one thread in a fixed order, so the
     // results do not depend on the split.  Both warps wait for the slab and
     // weight barriers; each commits its MMAs of a weight step to w_empty
-    // (two arrivals per phase), and warp 0 alone issues the weight copies.
+    // (two arrivals per phase), which the weight warp waits on to reuse the
+    // step's buffer.
     //
     // Cone pass, layer l - 1 -> l with a wider window (a "wavefront"
     // hand-off): no slab-wide ready barrier; before issuing tile t of layer
